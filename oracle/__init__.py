@@ -1,0 +1,154 @@
+"""CPU oracle for the shallow-water Lax-Wendroff path (TEST INFRASTRUCTURE).
+
+Plain, slow, FP64 code that states what the GPU path must compute:
+  * the reflective halo fill, the x- and y-face half steps and the full-step
+    update of the two-step Lax-Wendroff scheme (Sec. 3, step equations;
+    Sec. 3.1, Fortran statements) -- in ``swe_oracle.c``;
+  * the FP64 mass and CFL time step (Sec. 3) -- in ``swe_oracle.c``;
+  * the 4x4 block-average restriction and the corrector network -- in
+    ``downsample.py`` and ``nn.py`` (numpy, FP64).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library; the two meet only in the seeded input generators of ``swe_inputs``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Callable, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+WALL_LEFT, WALL_RIGHT, WALL_BOTTOM, WALL_TOP = 1, 2, 4, 8
+WALL_ALL = 15
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load (building if needed) the oracle's C library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_max_threads.restype = ctypes.c_int
+        L.oracle_fill_halo.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.oracle_face_workspace.restype = ctypes.c_size_t
+        L.oracle_face_workspace.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [_dp] * 7
+        L.oracle_run.restype = ctypes.c_int
+        L.oracle_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 \
+            + [ctypes.c_int, _dp, _dp, _dp]
+        L.oracle_mass.restype = ctypes.c_double
+        L.oracle_mass.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+        L.oracle_cfl_dt.restype = ctypes.c_double
+        L.oracle_cfl_dt.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [_dp] * 3
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+def pad(a: np.ndarray) -> np.ndarray:
+    """Interior (ny, nx) -> (ny+2, nx+2) with a zero ghost ring."""
+    out = np.zeros((a.shape[0] + 2, a.shape[1] + 2), dtype=np.float64)
+    out[1:-1, 1:-1] = a
+    return out
+
+
+def fill_halo(H: np.ndarray, U: np.ndarray, V: np.ndarray, walls: int = WALL_ALL) -> None:
+    """Reflective ghost fill in place on padded arrays (see swe_oracle.c)."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    lib().oracle_fill_halo(nx, ny, walls, _ptr(H), _ptr(U), _ptr(V))
+
+
+def step_padded(H, U, V, dx, dy, dt, g):
+    """One step on padded arrays whose ghost ring is already filled.
+
+    Returns the padded outputs (ghost ring zero) and the six face arrays
+    (Hx, Ux, Vx of shape (ny, nx+1); Hy, Uy, Vy of shape (ny+1, nx))."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    L = lib()
+    oH, oU, oV = (np.zeros_like(H) for _ in range(3))
+    faces = np.zeros(L.oracle_face_workspace(nx, ny), dtype=np.float64)
+    L.oracle_step(nx, ny, dx, dy, dt, g, _ptr(H), _ptr(U), _ptr(V),
+                  _ptr(oH), _ptr(oU), _ptr(oV), _ptr(faces))
+    nfx, nfy = (nx + 1) * ny, nx * (ny + 1)
+    fx = [faces[k * nfx:(k + 1) * nfx].reshape(ny, nx + 1) for k in range(3)]
+    fy = [faces[3 * nfx + k * nfy:3 * nfx + (k + 1) * nfy].reshape(ny + 1, nx) for k in range(3)]
+    return (oH, oU, oV), fx, fy
+
+
+def run_padded(H, U, V, dx, dy, dt, g, n_steps, walls=WALL_ALL):
+    """n_steps in place on padded float64 arrays."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    rc = lib().oracle_run(nx, ny, walls, dx, dy, dt, g, int(n_steps), _ptr(H), _ptr(U), _ptr(V))
+    if rc != 0:
+        raise MemoryError("oracle_run could not allocate its buffers")
+
+
+def run(h, hu, hv, dx, dy, dt, g, n_steps):
+    """n_steps with reflective walls on interior arrays; returns interiors."""
+    H, U, V = pad(np.asarray(h, np.float64)), pad(np.asarray(hu, np.float64)), pad(np.asarray(hv, np.float64))
+    run_padded(H, U, V, dx, dy, dt, g, n_steps)
+    return H[1:-1, 1:-1].copy(), U[1:-1, 1:-1].copy(), V[1:-1, 1:-1].copy()
+
+
+def mass(h, dx, dy) -> float:
+    """FP64 mass sum(h) dx dy over an interior array."""
+    H = pad(np.asarray(h, np.float64))
+    return float(lib().oracle_mass(H.shape[1] - 2, H.shape[0] - 2, dx, dy, _ptr(H)))
+
+
+def cfl_dt(h, hu, hv, dx, dy, g, cfl) -> float:
+    """FP64 CFL time step over interior arrays."""
+    H, U, V = (pad(np.asarray(a, np.float64)) for a in (h, hu, hv))
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    return float(lib().oracle_cfl_dt(nx, ny, dx, dy, g, cfl, _ptr(H), _ptr(U), _ptr(V)))
+
+
+def run_window(ic: Callable[[Tuple[int, int, int, int]], Tuple[np.ndarray, np.ndarray, np.ndarray]],
+               nx: int, ny: int, window: Tuple[int, int, int, int],
+               dx, dy, dt, g, n_steps):
+    """Exact values on a window of a large grid after n_steps.
+
+    The scheme reads only the four edge neighbours of a cell, so after n
+    steps a cell depends only on cells at most n away (domain of dependence).
+    ``ic(w)`` evaluates the initial interior state on the 1-based inclusive
+    index rectangle w = (i0, i1, j0, j1).  The window is grown by n cells per
+    side (clipped at the walls), its outer ring holds the true neighbour
+    values on sides that are not walls, and the ordinary step runs on it with
+    reflective fill on the wall sides only.  Cells inside ``window`` are then
+    exactly those of the full-grid run (checked bitwise in the tests).
+    Returns (h, hu, hv) on the window, shape (j1-j0+1, i1-i0+1).
+    """
+    i0, i1, j0, j1 = window
+    n = int(n_steps)
+    a, b = max(1, i0 - n + 1), min(nx, i1 + n - 1)
+    c, d = max(1, j0 - n + 1), min(ny, j1 + n - 1)
+    walls = 0
+    walls |= WALL_LEFT if a == 1 else 0
+    walls |= WALL_RIGHT if b == nx else 0
+    walls |= WALL_BOTTOM if c == 1 else 0
+    walls |= WALL_TOP if d == ny else 0
+    fields = ic((a - 1, b + 1, c - 1, d + 1))
+    H, U, V = (np.ascontiguousarray(f, dtype=np.float64) for f in fields)
+    run_padded(H, U, V, dx, dy, dt, g, n, walls)
+    sl = (slice(j0 - c + 1, j1 - c + 2), slice(i0 - a + 1, i1 - a + 2))
+    return H[sl].copy(), U[sl].copy(), V[sl].copy()
