@@ -1,0 +1,382 @@
+"""Benchmark: shallow-water Lax-Wendroff cell-updates/s on one 8192x8192 FP32
+grid (h = 1 + 64 Gaussian bumps, reflective walls, dt from CFL 0.2 at t = 0).
+
+One "step" is one time step of the whole path: reflective walls, x- and
+y-face half steps and the full-step update (one fused kernel launch).  The
+timed job is: FP64 CFL time step at t = 0, K steps, FP64 mass check.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs its own 8192x8192 replica ("replicas
+only": the grids are independent) and rank 0 prints the aggregate.  The
+reference arm times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+G = 9.80
+N_GRID = 8192
+CFL = 0.2
+BYTES_PER_CELL_F32 = 24  # read h, hu, hv + write h, hu, hv (FP32)
+METRIC = "SWE cell-updates/s, % HBM roofline; learned-coarse vs plain at equal error"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
+    p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(n, steps):
+    return {
+        "workload": "single %dx%d FP32 shallow-water grid, h = 1 + 64 Gaussian bumps (amp U[0.05,0.5], "
+                    "sigma U[8,64] cells, seed 1), hu = hv = 0, reflective walls, dx = dy = 1, g = 9.8, "
+                    "dt = FP64 CFL 0.2 at t = 0, two-step Lax-Wendroff" % (n, n),
+        "nx": n, "ny": n, "steps_timed": steps,
+        "job": "FP64 CFL dt + K steps + FP64 mass check",
+        "l2": "no flush: the state (3 x %d MB per buffer) is larger than L2 (129 MB)" % (n * n * 4 // 2**20),
+        "parallelism": "replicas (one independent grid per GPU)",
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1107_2157_gb300/csrc/swe_step.cu", "paper_1107_2157_gb300/csrc/swe_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel_name, cells):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel_name]
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["bytes_per_cell"] * cells
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(target_s=10.0, max_cells=2048 * 2048):
+    """Time the FP64 oracle on all host cores on a window of the 8192x8192
+    initial state.  Returns (cell-updates/s, threads, description)."""
+    import numpy as np
+    import oracle
+    import swe_inputs as si
+
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    m = int(math.sqrt(max_cells))
+    c0 = N_GRID // 2 - m // 2
+    st = si.large_grid_state(seed=1, n=N_GRID, window=(c0 + 1, c0 + m, c0 + 1, c0 + m))
+    H, U, V = (oracle.pad(a) for a in (st.h, st.hu, st.hv))
+    dt = oracle.cfl_dt(st.h, st.hu, st.hv, 1.0, 1.0, G, CFL)
+    t0 = time.perf_counter()
+    oracle.run_padded(H, U, V, 1.0, 1.0, dt, G, 1)
+    one = max(time.perf_counter() - t0, 1e-4)
+    steps = max(1, int(target_s / one))
+    t0 = time.perf_counter()
+    oracle.run_padded(H, U, V, 1.0, 1.0, dt, G, steps)
+    el = time.perf_counter() - t0
+    rate = m * m * steps / el
+    desc = ("FP64 C oracle (OpenMP over rows), %dx%d central window of the 8192x8192 initial state "
+            "with reflective walls, %d steps in %.1f s" % (m, m, steps, el))
+    return rate, threads, desc
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import swe_inputs as si
+
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    # size the per-step sample so that warmup + K steps take about a minute
+    m = 1024
+    c0 = N_GRID // 2 - m // 2
+    st = si.large_grid_state(seed=1, n=N_GRID, window=(c0 + 1, c0 + m, c0 + 1, c0 + m))
+    H, U, V = (oracle.pad(a) for a in (st.h, st.hu, st.hv))
+    dt = oracle.cfl_dt(st.h, st.hu, st.hv, 1.0, 1.0, G, CFL)
+    t0 = time.perf_counter()
+    oracle.run_padded(H, U, V, 1.0, 1.0, dt, G, 2)
+    per_cell = (time.perf_counter() - t0) / (2 * m * m)
+    budget = 60.0
+    cells = budget / max(per_cell, 1e-12) / max(1, args.steps + args.warmup)
+    m = int(max(64, min(2048, math.sqrt(cells))))
+    c0 = N_GRID // 2 - m // 2
+    st = si.large_grid_state(seed=1, n=N_GRID, window=(c0 + 1, c0 + m, c0 + 1, c0 + m))
+    H, U, V = (oracle.pad(a) for a in (st.h, st.hu, st.hv))
+    oracle.run_padded(H, U, V, 1.0, 1.0, dt, G, args.warmup)
+    t0 = time.perf_counter()
+    oracle.run_padded(H, U, V, 1.0, 1.0, dt, G, args.steps)
+    el = time.perf_counter() - t0
+    value = m * m * args.steps / el
+    sample = ("%dx%d central window of the %dx%d initial state (reflective walls), FP64 oracle, "
+              "%d timed steps" % (m, m, N_GRID, N_GRID, args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.n, args.steps),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import Grid, swe
+
+    n = args.n
+    cells = n * n
+    st = si.large_grid_state(seed=1 + rank, n=n)
+    h_host = torch.from_numpy(st.h.astype(np.float32)).pin_memory()
+    z_host = torch.zeros_like(h_host).pin_memory()
+    del st
+    h_dev = h_host.to("cuda")
+    z_dev = torch.zeros_like(h_dev)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    grid = Grid(n, n, 1.0, 1.0, 0.01, G, dtype="f32", kernel=args.kernel)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # --- warm-up -------------------------------------------------------------------------
+    grid.set_state(h_dev, z_dev, z_dev, stream=sp)
+    dt = grid.cfl_dt(CFL, stream=sp)
+    grid.set_dt(dt)
+    grid.step(args.warmup, stream=sp)
+    grid.mass(stream=sp)
+
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+
+    # --- timed job: device-resident inputs ---------------------------------------------------
+    grid.set_state(h_dev, z_dev, z_dev, stream=sp)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    launches0 = grid.query(swe.SWE_Q_LAUNCHES)
+    e0.record(stream)
+    dt = grid.cfl_dt(CFL, stream=sp)
+    grid.set_dt(dt)
+    e1.record(stream)
+    grid.step(args.steps, stream=sp)
+    e2.record(stream)
+    mass = grid.mass(stream=sp)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches = grid.query(swe.SWE_Q_LAUNCHES) - launches0
+    t_job = e0.elapsed_time(e3) / 1e3
+    t_steps = e1.elapsed_time(e2) / 1e3
+    status = grid.check(stream=sp)
+
+    # --- end-to-end through the C ABI with pinned host buffers ---------------------------------
+    out_host = [torch.empty_like(h_host).pin_memory() for _ in range(3)]
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    grid.set_state(h_host, z_host, z_host, stream=sp)
+    dt2 = grid.cfl_dt(CFL, stream=sp)
+    grid.set_dt(dt2)
+    grid.step(args.steps, stream=sp)
+    mass2 = grid.mass(stream=sp)
+    grid.get_state(out=out_host, stream=sp, sync=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_e2e = f0.elapsed_time(f1) / 1e3
+    clocks = sampler.stop() if sampler else None
+
+    # max over ranks
+    times = torch.tensor([t_job, t_steps, t_e2e], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    t_job, t_steps, t_e2e = (float(x) for x in times.tolist())
+    grid.close()
+    if rank != 0:
+        return
+
+    value = ws * cells * args.steps / t_job
+    per_launch = t_steps / max(1, launches)
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_CELL_F32 * cells / per_launch / 1e9
+    tr = traffic_per_launch("lw_tiled_kernel<float>", cells)
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        rate, thr, desc = cpu_oracle_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(n, args.steps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": tr,
+                     "kernel": "lw_tiled_kernel<float> (one launch per step)",
+                     "algorithmic_bytes_per_launch": BYTES_PER_CELL_F32 * cells,
+                     "launch_ms": per_launch * 1e3, "peak_source": peak_kind + " hbm_gbs (copy)"},
+        "e2e": {"value": ws * cells * args.steps / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": 3 * 4 * cells / args.steps, "d2h_bytes_per_step": 3 * 4 * cells / args.steps,
+                "note": "the job through the C ABI from pinned host buffers: host->device state (3 x FP32 "
+                        "planes), FP64 CFL dt, K steps, FP64 mass, device->host state; the state crosses "
+                        "once per K-step job, so the bytes per step are the plane bytes / K"},
+        "gpu_launches": int(launches) + 4,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "checks": {"status": swe.strerror(status), "mass": mass, "mass_e2e": mass2, "dt": dt},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        try:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+// swe_device.cuh -- device helpers shared by the stencil kernels: inline PTX
+// for mbarriers and TMA tile loads, bounded waits, and the shallow-water flux
+// algebra of the two-step Lax-Wendroff scheme (Sec. 3).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swe_internal.h"
+
+namespace swe {
+
+// ---------------------------------------------------------------------------
+// Bounded waits.  Every spin in this library gives up after this many
+// nanoseconds of %globaltimer, records SWE_ETIMEOUT in the error word and
+// lets the kernel return.
+// ---------------------------------------------------------------------------
+#ifndef SWE_WAIT_LIMIT_NS
+#define SWE_WAIT_LIMIT_NS 2000000000ull
+#endif
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes mbarrier initialisation visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase ``parity`` of ``bar`` to complete; gives up after
+// SWE_WAIT_LIMIT_NS, records SWE_ETIMEOUT in *err and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+{
+    for (int i = 0; i < 32; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > SWE_WAIT_LIMIT_NS) {
+            atomicExch(err, (int)SWE_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// 2D TMA tile load of the box at (x, y) of ``map`` into shared memory,
+// completing on ``bar`` (transaction bytes).  x * element size must be a
+// multiple of 16 bytes; out-of-range elements are filled with zeros.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic.  rcp(): FP32 uses the hardware approximate reciprocal
+// (rcp.approx, at most 1 ulp error); FP64 uses IEEE division.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+template <typename T>
+struct Coef {
+    T hx, hy;  // 0.5 dt/dx, 0.5 dt/dy: half-step factors (step 1)
+    T lx, ly;  // dt/dx, dt/dy: full-step factors (step 2)
+    T hg;      // g/2: the hydrostatic pressure g h^2 / 2
+};
+
+// A cell with its physical fluxes (Sec. 3 conservation laws):
+//   F = (U, U^2/H + g H^2/2, U V/H),  G = (V, U V/H, V^2/H + g H^2/2).
+// f3 doubles as G's second component (both are U V / H).
+template <typename T>
+struct CellQ {
+    T h, u, v;
+    T f2, f3, g3;
+};
+
+template <typename T>
+__device__ __forceinline__ CellQ<T> make_cell(T h, T u, T v, T hg)
+{
+    CellQ<T> c;
+    c.h = h;
+    c.u = u;
+    c.v = v;
+    const T inv = rcp(h);
+    const T p = hg * h * h;
+    const T uu = u * inv;
+    const T vv = v * inv;
+    c.f2 = fma(u, uu, p);
+    c.f3 = u * vv;
+    c.g3 = fma(v, vv, p);
+    return c;
+}
+
+// Mirror of a cell across an x-wall: U negated, H and V copied.
+template <typename T>
+__device__ __forceinline__ CellQ<T> mirror_x(const CellQ<T> &c)
+{
+    CellQ<T> m = c;
+    m.u = -c.u;
+    m.f3 = -c.f3;
+    return m;
+}
+
+// Mirror of a cell across a y-wall: V negated, H and U copied.
+template <typename T>
+__device__ __forceinline__ CellQ<T> mirror_y(const CellQ<T> &c)
+{
+    CellQ<T> m = c;
+    m.v = -c.v;
+    m.f3 = -c.f3;
+    return m;
+}
+
+template <typename T>
+struct Flux3 {
+    T a, b, c;
+};
+
+// Step 1 on an x-face between cells L (left) and R (right), then the
+// x-flux F evaluated at the face state (step 2's input).
+template <typename T>
+__device__ __forceinline__ Flux3<T> xface_flux(const CellQ<T> &L, const CellQ<T> &R, const Coef<T> &k)
+{
+    const T half = T(0.5);
+    const T Hf = fma(k.hx, L.u - R.u, half * (L.h + R.h));
+    const T Uf = fma(k.hx, L.f2 - R.f2, half * (L.u + R.u));
+    const T Vf = fma(k.hx, L.f3 - R.f3, half * (L.v + R.v));
+    const T inv = rcp(Hf);
+    const T uf = Uf * inv;
+    Flux3<T> F;
+    F.a = Uf;
+    F.b = fma(Uf, uf, k.hg * Hf * Hf);
+    F.c = Vf * uf;
+    return F;
+}
+
+// Step 1 on a y-face between cells D (below) and U (above), then the
+// y-flux G at the face state.
+template <typename T>
+__device__ __forceinline__ Flux3<T> yface_flux(const CellQ<T> &D, const CellQ<T> &U, const Coef<T> &k)
+{
+    const T half = T(0.5);
+    const T Hf = fma(k.hy, D.v - U.v, half * (D.h + U.h));
+    const T Uf = fma(k.hy, D.f3 - U.f3, half * (D.u + U.u));
+    const T Vf = fma(k.hy, D.g3 - U.g3, half * (D.v + U.v));
+    const T inv = rcp(Hf);
+    const T vf = Vf * inv;
+    Flux3<T> G;
+    G.a = Vf;
+    G.b = Uf * vf;
+    G.c = fma(Vf, vf, k.hg * Hf * Hf);
+    return G;
+}
+
+// Step 2: conservative update of one cell from its four face fluxes.
+template <typename T>
+__device__ __forceinline__ void lw_update(T &h, T &u, T &v, const Flux3<T> &Fl, const Flux3<T> &Fr,
+                                          const Flux3<T> &Gd, const Flux3<T> &Gu, const Coef<T> &k)
+{
+    h = fma(k.ly, Gd.a - Gu.a, fma(k.lx, Fl.a - Fr.a, h));
+    u = fma(k.ly, Gd.b - Gu.b, fma(k.lx, Fl.b - Fr.b, u));
+    v = fma(k.ly, Gd.c - Gu.c, fma(k.lx, Fl.c - Fr.c, v));
+}
+
+}  // namespace swe

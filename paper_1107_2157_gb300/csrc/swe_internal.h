@@ -1,0 +1,55 @@
+// swe_internal.h -- library-internal declarations shared by the .cu files
+// of the shallow-water library (not part of the C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/swe.h"
+
+namespace swe {
+
+// Device planes: ny rows of ``pitch`` elements, interior cell (i, j) at
+// j*pitch + i.  The pitch is a multiple of 128 bytes so that every row
+// starts on a 128-byte boundary (TMA strides, 16-byte vector access).
+inline long long plane_pitch(int nx, size_t esize)
+{
+    const long long per = 128 / (long long)esize;
+    return ((long long)nx + per - 1) / per * per;
+}
+
+// Step-kernel launch geometry of one variant.
+struct StepGeom {
+    int tile_x, tile_y;  // output cells per CTA
+    int threads;         // threads per CTA
+    size_t smem;         // dynamic shared memory, bytes
+};
+
+// Launchers implemented in swe_step.cu.  ``in``/``out`` each point to three
+// planes (H, U, V) of ``plane`` elements.  All return cudaError_t of the
+// launch.
+cudaError_t launch_naive(int dtype, const void *in, void *out, size_t plane, int nx, int ny, long long pitch,
+                         double dx, double dy, double dt, double g, cudaStream_t s);
+cudaError_t launch_tiled(int dtype, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
+                         long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+StepGeom tiled_geom(int dtype);
+void tiled_box(int dtype, int *bw, int *bh);  // TMA box the tiled kernel loads
+
+// Reductions implemented in swe_reduce.cu.  ``scratch`` holds at least
+// reduce_scratch_doubles() doubles; results land in out_dev[0..1].
+size_t reduce_scratch_doubles();
+cudaError_t launch_mass(int dtype, const void *H, int nx, int ny, long long pitch, double dxdy, double *scratch,
+                        double *out_dev, cudaStream_t s);
+cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, int nx, int ny, long long pitch,
+                       double dx, double dy, double g, double cfl, double *scratch, double *out_dev,
+                       cudaStream_t s);
+
+// TMA descriptor encoding through the driver entry point (no -lcuda link).
+// Encodes a 2D map over an nx x ny plane with the given box; returns false
+// if the driver entry point is unavailable or the encode fails.
+bool encode_plane_map(CUtensorMap *map, int dtype, const void *base, int nx, int ny, long long pitch, int box_x,
+                      int box_y);
+
+}  // namespace swe

@@ -1,0 +1,248 @@
+"""ctypes binding of the C ABI in include/swe.h (argument marshalling only).
+
+Every ``swe_*`` function here calls the function of the same name in
+libswe.so; no step of the method runs in Python.  ``Grid`` is a small
+convenience wrapper that owns a context handle and marshals numpy arrays
+(host) or torch tensors (host or device) into pointer/stride arguments.
+
+Loading fails loudly if libswe.so is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswe.so")
+
+SWE_OK, SWE_EINVAL, SWE_ENOMEM, SWE_ECUDA, SWE_ETIMEOUT, SWE_ECHECK, SWE_EUNSUPPORTED = range(7)
+SWE_F32, SWE_F64 = 0, 1
+SWE_KERNEL_AUTO, SWE_KERNEL_NAIVE, SWE_KERNEL_TILED, SWE_KERNEL_TEMPORAL = range(4)
+(SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
+ SWE_Q_STATE_PTR) = range(7)
+
+
+class SweError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (where, strerror(status), status))
+
+
+class swe_options(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("kernel", ctypes.c_int), ("depth", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+_vp = ctypes.c_void_p
+_i, _d, _ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "swe_options_init": (None, [ctypes.POINTER(swe_options)]),
+    "swe_create": (_i, [_i, _i, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
+    "swe_create_ex": (_i, [_i, _i, _d, _d, _d, _d, ctypes.POINTER(swe_options), ctypes.POINTER(_vp)]),
+    "swe_destroy": (None, [_vp]),
+    "swe_set_dt": (_i, [_vp, _d]),
+    "swe_set_state": (_i, [_vp, _vp, _vp, _vp, _ll, _i, _vp]),
+    "swe_get_state": (_i, [_vp, _vp, _vp, _vp, _ll, _i, _vp]),
+    "swe_step": (_i, [_vp, _i, _vp]),
+    "swe_mass": (_i, [_vp, ctypes.POINTER(_d), _vp]),
+    "swe_cfl_dt": (_i, [_vp, _d, ctypes.POINTER(_d), _vp]),
+    "swe_check": (_i, [_vp, _vp]),
+    "swe_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
+    "swe_strerror": (ctypes.c_char_p, [_i]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libswe.so (built by paper_1107_2157_gb300.build / build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libswe.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().swe_strerror(int(status)).decode()
+    except Exception:  # pragma: no cover
+        return "status %d" % status
+
+
+def check(status: int, where: str) -> None:
+    if status != SWE_OK:
+        raise SweError(status, where)
+
+
+# --- the C ABI under its own names --------------------------------------------------
+
+def swe_options_init() -> swe_options:
+    o = swe_options()
+    lib().swe_options_init(ctypes.byref(o))
+    return o
+
+
+def swe_create(nx, ny, dx, dy, dt, g) -> int:
+    h = _vp()
+    check(lib().swe_create(nx, ny, dx, dy, dt, g, ctypes.byref(h)), "swe_create")
+    return h.value
+
+
+def swe_create_ex(nx, ny, dx, dy, dt, g, opt: swe_options) -> int:
+    h = _vp()
+    check(lib().swe_create_ex(nx, ny, dx, dy, dt, g, ctypes.byref(opt), ctypes.byref(h)), "swe_create_ex")
+    return h.value
+
+
+def swe_destroy(ctx) -> None:
+    lib().swe_destroy(ctx)
+
+
+def swe_set_dt(ctx, dt) -> None:
+    check(lib().swe_set_dt(ctx, dt), "swe_set_dt")
+
+
+def swe_set_state(ctx, h, hu, hv, ld, on_device, stream=None) -> None:
+    check(lib().swe_set_state(ctx, h, hu, hv, ld, on_device, stream), "swe_set_state")
+
+
+def swe_get_state(ctx, h, hu, hv, ld, on_device, stream=None) -> None:
+    check(lib().swe_get_state(ctx, h, hu, hv, ld, on_device, stream), "swe_get_state")
+
+
+def swe_step(ctx, n_steps, stream=None) -> None:
+    check(lib().swe_step(ctx, int(n_steps), stream), "swe_step")
+
+
+def swe_mass(ctx, stream=None) -> float:
+    m = _d()
+    check(lib().swe_mass(ctx, ctypes.byref(m), stream), "swe_mass")
+    return m.value
+
+
+def swe_cfl_dt(ctx, cfl, stream=None) -> float:
+    d = _d()
+    check(lib().swe_cfl_dt(ctx, cfl, ctypes.byref(d), stream), "swe_cfl_dt")
+    return d.value
+
+
+def swe_check(ctx, stream=None) -> int:
+    return int(lib().swe_check(ctx, stream))
+
+
+def swe_query(ctx, key) -> int:
+    v = _ll()
+    check(lib().swe_query(ctx, int(key), ctypes.byref(v)), "swe_query")
+    return v.value
+
+
+# --- marshalling helpers -----------------------------------------------------------------
+
+def current_stream():
+    """cudaStream_t of torch's current stream (as an int), or None."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def _buf(a, dtype_np):
+    """(pointer, row stride in elements, on_device) of a 2D array/tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype_np or a.ndim != 2 or a.strides[1] != a.itemsize:
+            raise ValueError("expected a 2D %s array with unit x stride" % dtype_np)
+        return a.ctypes.data, a.strides[0] // a.itemsize, 0
+    import torch
+    if not isinstance(a, torch.Tensor) or a.dim() != 2 or a.stride(1) != 1:
+        raise ValueError("expected a 2D tensor with unit x stride")
+    want = torch.float32 if dtype_np == np.float32 else torch.float64
+    if a.dtype != want:
+        raise ValueError("tensor dtype %s, expected %s" % (a.dtype, want))
+    return a.data_ptr(), a.stride(0), 1 if a.is_cuda else 0
+
+
+class Grid:
+    """One nx x ny grid on the current CUDA device (owns a swe_ctx)."""
+
+    def __init__(self, nx, ny, dx, dy, dt, g, dtype="f32", kernel=SWE_KERNEL_AUTO, depth=0):
+        o = swe_options_init()
+        o.dtype = SWE_F64 if dtype in ("f64", np.float64) else SWE_F32
+        o.kernel = kernel
+        o.depth = depth
+        self.np_dtype = np.float64 if o.dtype == SWE_F64 else np.float32
+        self.nx, self.ny = nx, ny
+        self.ctx = swe_create_ex(nx, ny, dx, dy, dt, g, o)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            swe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, h, hu, hv, stream=None):
+        bufs = [_buf(a, self.np_dtype) for a in (h, hu, hv)]
+        if len({b[1] for b in bufs}) != 1 or len({b[2] for b in bufs}) != 1:
+            raise ValueError("h, hu, hv must share row stride and location")
+        swe_set_state(self.ctx, bufs[0][0], bufs[1][0], bufs[2][0], bufs[0][1], bufs[0][2],
+                      stream if stream is not None else current_stream())
+
+    def get_state(self, out=None, stream=None, sync=True):
+        """Copies the state to ``out`` (3 arrays/tensors) or new numpy arrays."""
+        if out is None:
+            out = [np.empty((self.ny, self.nx), self.np_dtype) for _ in range(3)]
+        bufs = [_buf(a, self.np_dtype) for a in out]
+        s = stream if stream is not None else current_stream()
+        swe_get_state(self.ctx, bufs[0][0], bufs[1][0], bufs[2][0], bufs[0][1], bufs[0][2], s)
+        if sync:
+            import torch
+            torch.cuda.synchronize()
+        return out
+
+    def step(self, n, stream=None):
+        swe_step(self.ctx, n, stream if stream is not None else current_stream())
+
+    def set_dt(self, dt):
+        swe_set_dt(self.ctx, dt)
+
+    def mass(self, stream=None):
+        return swe_mass(self.ctx, stream if stream is not None else current_stream())
+
+    def cfl_dt(self, cfl, stream=None):
+        return swe_cfl_dt(self.ctx, cfl, stream if stream is not None else current_stream())
+
+    def check(self, stream=None):
+        return swe_check(self.ctx, stream if stream is not None else current_stream())
+
+    def query(self, key):
+        return swe_query(self.ctx, key)

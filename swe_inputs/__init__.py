@@ -210,3 +210,18 @@ def corrector_training_state(seed: int, n: int = 1024, dam_fraction: float = 0.1
     if rng.uniform() < dam_fraction:
         return dam_break_state(seed, n)
     return _at_rest(bumps_h(n, n, 1.0, multi_bumps(seed, 7, n, n, bump_count)))
+
+
+def smooth_flow_state(seed: int, nx: int, ny: int, amp_u: float = 0.3) -> State:
+    """A smooth state with momentum in both directions (nonzero at the walls),
+    for edge and ragged-size tests: h = 1.5 + bumps, hu and hv sinusoidal."""
+    rng = SplitMix64(seed, 0x5F)
+    smax = max(1.5, min(nx, ny) / 4.0)
+    bumps = multi_bumps(seed, 0x60, nx, ny, 3, sigma_range=(1.0, smax))
+    h = bumps_h(nx, ny, 1.5, bumps)
+    x = (np.arange(nx, dtype=np.float64) + 0.5) / nx
+    y = (np.arange(ny, dtype=np.float64) + 0.5) / ny
+    a, b = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+    hu = amp_u * h * (np.cos(math.pi * a * y)[:, None] * np.cos(0.7 * math.pi * x)[None, :])
+    hv = amp_u * h * (np.sin(0.9 * math.pi * y)[:, None] * np.cos(math.pi * b * x)[None, :])
+    return State(h, hu, hv)

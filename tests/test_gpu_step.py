@@ -1,0 +1,202 @@
+"""GPU parity of the single-grid path (C ABI -> CUDA kernels) against the
+FP64 oracle, on the same seeded inputs.
+
+Bars: FP64 within 1e-12 relative per field, FP32 within 2e-5 (relative
+error as defined in tests/parity.py); integer-like facts (lake at rest, the
+CFL step) bitwise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import swe_inputs as si
+from parity import G, TOL_F32, TOL_F64, rel_errors, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = {"tiled": 2, "naive": 1}
+
+
+def _oracle(state, dx, dy, dt, n):
+    return oracle.run(state.h, state.hu, state.hv, dx, dy, dt, G, n)
+
+
+@pytest.mark.parametrize("seed", list(range(10)))
+def test_128_fp64_100_steps(seed):
+    """128x128 bump, FP64, dt from CFL 0.2 at t = 0, 100 steps."""
+    s = si.single_bump_state(seed)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.2)
+    ref = _oracle(s, 1.0, 1.0, dt, 100)
+    got = run_gpu(s, 1.0, 1.0, dt, G, 100, "f64")
+    errs = rel_errors(got, ref)
+    assert max(errs) <= TOL_F64, errs
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_128_fp32_100_steps(seed):
+    s = si.single_bump_state(seed)
+    s32 = s.rounded_to(np.float32)
+    dt = oracle.cfl_dt(s32.h, s32.hu, s32.hv, 1.0, 1.0, G, 0.2)
+    ref = _oracle(s32, 1.0, 1.0, dt, 100)
+    got = run_gpu(s32, 1.0, 1.0, dt, G, 100, "f32")
+    errs = rel_errors(got, ref)
+    assert max(errs) <= TOL_F32, errs
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "naive"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (9, 1), (3, 5), (4, 4), (127, 31), (129, 33),
+                                   (130, 66), (200, 97), (257, 129), (64, 200)])
+def test_ragged_sizes_with_flow_at_walls(kernel, dtype, nx, ny):
+    """Sizes below, at and just past tile multiples, with momentum at every
+    wall so the ghost rule is exercised on all four sides."""
+    s = si.smooth_flow_state(nx * 1000 + ny, nx, ny)
+    dx, dy = 0.8, 1.1
+    if dtype == "f32":
+        s = s.rounded_to(np.float32)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, dx, dy, G, 0.3)
+    ref = _oracle(s, dx, dy, dt, 20)
+    got = run_gpu(s, dx, dy, dt, G, 20, dtype, KERNELS[kernel])
+    errs = rel_errors(got, ref, floor_frac=1e-2)
+    assert max(errs) <= (TOL_F64 if dtype == "f64" else TOL_F32), errs
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_lake_at_rest_bitwise(dtype):
+    nx, ny = 300, 170
+    s = si.State(np.full((ny, nx), 1.7), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    got = run_gpu(s, 0.7, 1.1, 0.03, G, 1000, dtype)
+    assert np.array_equal(got[0], s.h.astype(got[0].dtype))
+    assert not np.any(got[1]) and not np.any(got[2])
+
+
+def test_zero_steps_round_trip_is_exact():
+    s = si.smooth_flow_state(5, 77, 45)
+    for dtype, npd in (("f32", np.float32), ("f64", np.float64)):
+        got = run_gpu(s, 1.0, 1.0, 0.01, G, 0, dtype)
+        for k, a in enumerate((s.h, s.hu, s.hv)):
+            assert np.array_equal(got[k], a.astype(npd))
+
+
+def test_mirror_symmetry_fp64():
+    s = si.single_bump_state(0, centred=True)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.2)
+    h, hu, hv = run_gpu(s, 1.0, 1.0, dt, G, 100, "f64")
+    scale = np.abs(h).max()
+    assert np.abs(h - h[:, ::-1]).max() <= 1e-13 * scale
+    assert np.abs(hu + hu[:, ::-1]).max() <= 1e-13 * scale
+    assert np.abs(h - h[::-1, :]).max() <= 1e-13 * scale
+    assert np.abs(hv + hv[::-1, :]).max() <= 1e-13 * scale
+
+
+# ---------------------------------------------------------------------------
+# FP64 reductions
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_mass_and_cfl_match_oracle(dtype):
+    from paper_1107_2157_gb300 import Grid
+    nx, ny, dx, dy = 517, 389, 0.6, 1.3
+    s = si.smooth_flow_state(17, nx, ny)
+    npd = np.float32 if dtype == "f32" else np.float64
+    s = s.rounded_to(npd)
+    with Grid(nx, ny, dx, dy, 0.01, G, dtype=dtype) as grid:
+        grid.set_state(*(a.astype(npd) for a in (s.h, s.hu, s.hv)))
+        m = grid.mass()
+        dt = grid.cfl_dt(0.2)
+    m_ref = oracle.mass(s.h, dx, dy)
+    assert abs(m - m_ref) <= 1e-14 * m_ref
+    # the per-cell bounds are correctly rounded FP64 operations on both sides
+    assert dt == oracle.cfl_dt(s.h, s.hu, s.hv, dx, dy, G, 0.2)
+
+
+def test_cfl_rejects_non_positive_depth():
+    from paper_1107_2157_gb300 import Grid, SweError
+    s = si.smooth_flow_state(3, 40, 30)
+    h = s.h.copy()
+    h[7, 11] = 0.0
+    with Grid(40, 30, 1.0, 1.0, 0.01, G, dtype="f64") as grid:
+        grid.set_state(h, s.hu, s.hv)
+        with pytest.raises(SweError) as e:
+            grid.cfl_dt(0.2)
+        assert e.value.status == 5  # SWE_ECHECK
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_mass_conservation_on_gpu(dtype):
+    from paper_1107_2157_gb300 import Grid
+    s = si.single_bump_state(4)
+    npd = np.float32 if dtype == "f32" else np.float64
+    with Grid(128, 128, 1.0, 1.0, 0.04, G, dtype=dtype) as grid:
+        grid.set_state(*(a.astype(npd) for a in (s.h, s.hu, s.hv)))
+        m0 = grid.mass()
+        grid.step(100)
+        m1 = grid.mass()
+    drift = abs(m1 - m0) / m0
+    assert drift <= (1e-13 if dtype == "f64" else 1e-6), drift
+
+
+# ---------------------------------------------------------------------------
+# Full size, in the launch configuration the benchmark times
+# ---------------------------------------------------------------------------
+
+N_FULL = 8192
+
+
+def _full_windows(n, w=8, seed=12):
+    rng = np.random.default_rng(seed)
+    corners = [(1, w, 1, w), (n - w + 1, n, 1, w), (1, w, n - w + 1, n), (n - w + 1, n, n - w + 1, n)]
+    edges = [(n // 2, n // 2 + w - 1, 1, w), (1, w, n // 3, n // 3 + w - 1),
+             (n - w + 1, n, 2 * n // 3, 2 * n // 3 + w - 1), (n // 5, n // 5 + w - 1, n - w + 1, n)]
+    inner = []
+    for _ in range(4):
+        i0, j0 = (int(v) for v in rng.integers(200, n - 200, 2))
+        inner.append((i0, i0 + w - 1, j0, j0 + w - 1))
+    # tile seams of the 128x32 (FP32) and 64x32 (FP64) tiles
+    seams = [(128 * 20 - 3, 128 * 20 + 4, 32 * 50 - 3, 32 * 50 + 4)]
+    return corners + edges + inner + seams
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_full_size_8192_sampled_windows(dtype):
+    """8192x8192, 64 bumps: GPU after 100 steps vs exact oracle values on
+    sampled windows (domain of dependence), plus mass and positivity after
+    1000 steps."""
+    from paper_1107_2157_gb300 import Grid
+    n, steps = N_FULL, 100
+    npd = np.float32 if dtype == "f32" else np.float64
+    full = si.large_grid_state(seed=1, n=n)
+    h0 = full.h.astype(npd)
+    z = np.zeros_like(h0)
+    with Grid(n, n, 1.0, 1.0, 0.01, G, dtype=dtype) as grid:
+        grid.set_state(h0, z, z)
+        dt = grid.cfl_dt(0.2)
+        grid.set_dt(dt)
+        m0 = grid.mass()
+        grid.step(steps)
+        got = grid.get_state()
+        grid.step(1000 - steps)
+        m1 = grid.mass()
+        hlast = grid.get_state()[0]
+        assert grid.check() == 0
+    del full
+
+    def ic(w):
+        h = si.large_grid_state(seed=1, n=n, window=w).h.astype(npd).astype(np.float64)
+        return h, np.zeros_like(h), np.zeros_like(h)
+
+    tol = TOL_F64 if dtype == "f64" else TOL_F32
+    scale_h = float(h0.max())
+    floor = 1e-3 * scale_h * math.sqrt(G * scale_h)
+    for w in _full_windows(n):
+        ref = oracle.run_window(ic, n, n, w, 1.0, 1.0, dt, G, steps)
+        i0, i1, j0, j1 = w
+        for k in range(3):
+            sub = np.asarray(got[k][j0 - 1:j1, i0 - 1:i1], np.float64)
+            den = scale_h if k == 0 else floor
+            err = np.abs(sub - ref[k]).max() / den
+            assert err <= tol, (w, k, err)
+    assert np.isfinite(hlast).all() and hlast.min() > 0
+    assert abs(m1 - m0) / m0 <= (1e-13 if dtype == "f64" else 1e-5)
