@@ -145,6 +145,40 @@ typedef enum {
 /* Writes the value of ``key`` to *value. */
 swe_status swe_query(swe_ctx *ctx, int key, long long *value);
 
+/*
+ * swe_mass_noalloc: the FP64 mass sum(h) * dx * dy of a caller-owned device
+ * plane, computed without allocating anything.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: programs whose device memory is all owned by another
+ * allocator (a framework's caching pool that has reserved the GPU, so an
+ * extra cudaMalloc may fail or fragment it), and loops that cannot afford
+ * the device-wide synchronisation cudaMalloc/cudaFree may cause.  Such a
+ * caller has no swe_ctx (creating one allocates), only its own buffers.
+ *
+ * h: device pointer to nx x ny elements of ``dtype`` (SWE_F32 or SWE_F64),
+ * row stride ld >= nx elements.  mass_dev: device pointer to one double that
+ * receives the result.  Both stay owned by the caller.  Enqueued on
+ * ``stream``; the result is the same FP64 fixed-order sum swe_mass computes
+ * for the same data.
+ *
+ * Scratch: the partial sums live in a file-scope __device__ array of 1024
+ * doubles (8 KB), which every GPU that loads the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current); make the first
+ * call on each device before any stream capture.  All calls share the
+ * array and each call overwrites every partial it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU (other streams, other host
+ * threads) race on it: serialise them.
+ *
+ * Returns SWE_EINVAL for a bad dtype, a NULL pointer, ld < nx, dx or dy not
+ * finite and positive, or nx or ny outside 1..SWE_NOALLOC_MAX_DIM; SWE_ECUDA
+ * if the address lookup or the launch fails.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call.
+ */
+#define SWE_NOALLOC_MAX_DIM 65536
+swe_status swe_mass_noalloc(int dtype, const void *h, int nx, int ny, long long ld, double dx, double dy,
+                            double *mass_dev, void *stream);
+
 /* Static description of a status code. */
 const char *swe_strerror(swe_status s);
 

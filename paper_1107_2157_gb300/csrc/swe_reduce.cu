@@ -151,3 +151,57 @@ cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, i
 }
 
 }  // namespace swe
+
+// ---------------------------------------------------------------------------
+// swe_mass_noalloc: the mass reduction above with its partial sums in a
+// file-scope device array instead of a context's cudaMalloc'd scratch, for
+// callers that may not allocate device memory.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace swe {
+
+// One partial sum per block of mass_partial_kernel (at most kRedBlocks).
+static __device__ __align__(256) double g_noalloc_partials[kRedBlocks];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_partials on the current device, looked up
+// once per device.  In host code the array's name is only a host-side
+// stand-in, so the kernels must be given this address.
+static cudaError_t noalloc_partials(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace swe
+
+extern "C" swe_status swe_mass_noalloc(int dtype, const void *h, int nx, int ny, long long ld, double dx, double dy,
+                                       double *mass_dev, void *stream)
+{
+    using namespace swe;
+    if (dtype != SWE_F32 && dtype != SWE_F64) return SWE_EINVAL;
+    if (!h || !mass_dev) return SWE_EINVAL;
+    if (nx < 1 || ny < 1 || nx > SWE_NOALLOC_MAX_DIM || ny > SWE_NOALLOC_MAX_DIM || ld < nx) return SWE_EINVAL;
+    if (!(dx > 0.0) || !(dy > 0.0) || !isfinite(dx) || !isfinite(dy)) return SWE_EINVAL;
+    double *partials = nullptr;
+    cudaError_t e = noalloc_partials(&partials);
+    if (e != cudaSuccess) return SWE_ECUDA;
+    // every partial the final kernel reads is written first: nothing to clear
+    e = launch_mass(dtype, h, nx, ny, ld, dx * dy, partials, mass_dev, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SWE_OK : SWE_ECUDA;
+}

@@ -55,6 +55,7 @@ _SIGS = {
     "swe_check": (_i, [_vp, _vp]),
     "swe_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_strerror": (ctypes.c_char_p, [_i]),
+    "swe_mass_noalloc": (_i, [_i, _vp, _i, _i, _ll, _d, _d, _vp, _vp]),
 }
 
 
@@ -151,6 +152,13 @@ def swe_query(ctx, key) -> int:
     v = _ll()
     check(lib().swe_query(ctx, int(key), ctypes.byref(v)), "swe_query")
     return v.value
+
+
+def swe_mass_noalloc(dtype, h, nx, ny, ld, dx, dy, mass_dev, stream=None) -> None:
+    """FP64 mass of a caller-owned device plane into ``mass_dev`` (device
+    pointer to one double); allocates nothing (see include/swe.h)."""
+    check(lib().swe_mass_noalloc(int(dtype), h, int(nx), int(ny), int(ld), dx, dy, mass_dev, stream),
+          "swe_mass_noalloc")
 
 
 # --- marshalling helpers -----------------------------------------------------------------
