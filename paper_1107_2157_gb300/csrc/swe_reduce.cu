@@ -15,7 +15,7 @@ namespace swe {
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
-size_t reduce_scratch_doubles() { return 2 * (size_t)kRedBlocks + 16; }
+size_t reduce_scratch_doubles() { return 5 * (size_t)kRedBlocks + 16; }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -31,32 +31,65 @@ __device__ __forceinline__ double warp_min(double v)
     return v;
 }
 
-// Block-wide sum / min; every thread gets the result.
-template <bool MIN>
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reduction (sum, or min / max of non-negative values when MIN /
+// MAX is set); every thread gets the result.
+template <bool MIN, bool MAX = false>
 __device__ double block_reduce(double v)
 {
     __shared__ double part[32];
-    v = MIN ? warp_min(v) : warp_sum(v);
+    v = MIN ? warp_min(v) : (MAX ? warp_max(v) : warp_sum(v));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) part[w] = v;
     __syncthreads();
     const int nw = (blockDim.x + 31) >> 5;
     v = (lane < nw) ? part[lane] : (MIN ? __longlong_as_double(0x7ff0000000000000ll) : 0.0);
-    v = MIN ? warp_min(v) : warp_sum(v);
+    v = MIN ? warp_min(v) : (MAX ? warp_max(v) : warp_sum(v));
     __syncthreads();
     return v;
 }
 
-template <typename T>
+// Mass partials.  Each block takes rows blockIdx.x, blockIdx.x + gridDim.x,
+// ...; with VEC the threads read 16-byte vectors (4 FP32 / 2 FP64 values,
+// the row base and stride being 16-byte aligned) and the row tail scalar.
+// Two FP64 accumulators per thread keep the adds independent.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) mass_partial_kernel(const T *__restrict__ H, int nx, int ny,
                                                                    long long pitch, double *partial)
 {
-    double s = 0.0;
+    constexpr int N = 16 / sizeof(T);
+    double s0 = 0.0, s1 = 0.0;
     for (int j = blockIdx.x; j < ny; j += gridDim.x) {
         const T *row = H + (size_t)j * (size_t)pitch;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) s += (double)row[i];
+        int i0 = 0;
+        if (VEC) {
+            const int nv = nx / N;
+            const T *base = row;
+#pragma unroll 4
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 x = __ldg(reinterpret_cast<const float4 *>(base) + v);
+                    s0 += (double)x.x;
+                    s1 += (double)x.y;
+                    s0 += (double)x.z;
+                    s1 += (double)x.w;
+                } else {
+                    const double2 x = __ldg(reinterpret_cast<const double2 *>(base) + v);
+                    s0 += (double)x.x;
+                    s1 += (double)x.y;
+                }
+            }
+            i0 = nv * N;
+        }
+        for (int i = i0 + threadIdx.x; i < nx; i += blockDim.x) s0 += (double)row[i];
     }
-    s = block_reduce<false>(s);
+    const double s = block_reduce<false>(s0 + s1);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -68,52 +101,145 @@ __global__ void __launch_bounds__(1024) sum_final_kernel(const double *partial, 
     if (threadIdx.x == 0) out[0] = s * scale;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) cfl_partial_kernel(const T *__restrict__ H, const T *__restrict__ U,
-                                                                  const T *__restrict__ V, int nx, int ny,
-                                                                  long long pitch, double dx, double dy, double g,
-                                                                  double *pmin, double *pbad)
+// ---------------------------------------------------------------------------
+// CFL time step.  dt = cfl * min over cells of min(dx / sx, dy / sy) with
+// sx = sqrt(g h) + |hu / h|, sy = sqrt(g h) + |hv / h|, all FP64.  A correctly
+// rounded division is monotone, so min over cells of fl(dx / sx) equals
+// fl(dx / max sx): only the exact FP64 maxima Sx, Sy are needed.  GB300's
+// FP64 units are slow, so pass 1 finds FP32 estimates of the maxima (relative
+// error far below 2^-16) and pass 2 evaluates the exact FP64 sx, sy only for
+// cells whose estimate lies within 2^-16 of the estimated maximum; no other
+// cell can hold the maximum.  A thread reuses its last exact value when it
+// meets the same (h, momentum) bits again, so flat regions cost one FP64
+// evaluation per thread.
+// ---------------------------------------------------------------------------
+constexpr float kCflSlack = 1.0f / 65536.0f;
+
+__device__ __forceinline__ bool cell_bad(double h, double u, double v)
 {
-    double best = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    return !(h > 0.0) || !isfinite(h) || !isfinite(u) || !isfinite(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(const T *__restrict__ H, const T *__restrict__ U,
+                                                                const T *__restrict__ V, int nx, int ny,
+                                                                long long pitch, float g32, double *scratch)
+{
+    float ax = 0.0f, ay = 0.0f;
     double bad = 0.0;
     for (int j = blockIdx.x; j < ny; j += gridDim.x) {
         const size_t ro = (size_t)j * (size_t)pitch;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            const double h = (double)H[ro + i];
-            const double u = (double)U[ro + i];
-            const double v = (double)V[ro + i];
-            if (!(h > 0.0) || !isfinite(h) || !isfinite(u) || !isfinite(v)) {
+            const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
+            if (cell_bad((double)h, (double)u, (double)v)) {
                 bad += 1.0;
                 continue;
             }
-            const double c = __dsqrt_rn(__dmul_rn(g, h));
-            const double tx = __ddiv_rn(dx, __dadd_rn(c, fabs(__ddiv_rn(u, h))));
-            const double ty = __ddiv_rn(dy, __dadd_rn(c, fabs(__ddiv_rn(v, h))));
-            best = fmin(best, fmin(tx, ty));
+            const float hf = (float)h;
+            const float inv = rcp(hf);
+            const float c = sqrtf(g32 * hf);
+            ax = fmaxf(ax, c + fabsf((float)u * inv));
+            ay = fmaxf(ay, c + fabsf((float)v * inv));
         }
     }
-    best = block_reduce<true>(best);
-    bad = block_reduce<false>(bad);
+    ax = (float)block_reduce<false, true>((double)ax);
+    ay = (float)block_reduce<false, true>((double)ay);
+    bad = block_reduce<false, false>(bad);
     if (threadIdx.x == 0) {
-        pmin[blockIdx.x] = best;
-        pbad[blockIdx.x] = bad;
+        scratch[blockIdx.x] = ax;
+        scratch[kRedBlocks + blockIdx.x] = ay;
+        scratch[2 * kRedBlocks + blockIdx.x] = bad;
     }
 }
 
-__global__ void __launch_bounds__(1024) cfl_final_kernel(const double *pmin, const double *pbad, int n, double cfl,
-                                                         double *out)
+// Combines pass-1 partials into the pass-2 thresholds (scratch[3K..3K+2]).
+__global__ void __launch_bounds__(1024) cfl_pass1_final_kernel(double *scratch, int n)
 {
-    double best = __longlong_as_double(0x7ff0000000000000ll);
-    double bad = 0.0;
+    double ax = 0.0, ay = 0.0, bad = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        best = fmin(best, pmin[i]);
-        bad += pbad[i];
+        ax = fmax(ax, scratch[i]);
+        ay = fmax(ay, scratch[kRedBlocks + i]);
+        bad += scratch[2 * kRedBlocks + i];
     }
-    best = block_reduce<true>(best);
-    bad = block_reduce<false>(bad);
+    ax = block_reduce<false, true>(ax);
+    ay = block_reduce<false, true>(ay);
+    bad = block_reduce<false, false>(bad);
     if (threadIdx.x == 0) {
-        out[0] = __dmul_rn(cfl, best);
-        out[1] = bad;
+        // a non-finite or tiny estimate disables the filter (every cell exact)
+        const double lo = -1.0;
+        scratch[3 * kRedBlocks + 0] = (isfinite(ax) && ax > 1e-30) ? ax * (1.0 - (double)kCflSlack) : lo;
+        scratch[3 * kRedBlocks + 1] = (isfinite(ay) && ay > 1e-30) ? ay * (1.0 - (double)kCflSlack) : lo;
+        scratch[3 * kRedBlocks + 2] = bad;
+    }
+}
+
+// Exact FP64 sx or sy of one cell, every operation correctly rounded.
+__device__ __forceinline__ double exact_speed(double g, double h, double m)
+{
+    return __dadd_rn(__dsqrt_rn(__dmul_rn(g, h)), fabs(__ddiv_rn(m, h)));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(const T *__restrict__ H, const T *__restrict__ U,
+                                                                const T *__restrict__ V, int nx, int ny,
+                                                                long long pitch, float g32, double g,
+                                                                double *scratch)
+{
+    const double thx = scratch[3 * kRedBlocks + 0];
+    const double thy = scratch[3 * kRedBlocks + 1];
+    double sx = 0.0, sy = 0.0;
+    T lhx = T(-1), lux = T(0), lhy = T(-1), lvy = T(0);  // last exactly evaluated inputs
+    double lsx = 0.0, lsy = 0.0;
+    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+        const size_t ro = (size_t)j * (size_t)pitch;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
+            if (cell_bad((double)h, (double)u, (double)v)) continue;
+            const float hf = (float)h;
+            const float inv = rcp(hf);
+            const float c = sqrtf(g32 * hf);
+            const double ex = (double)(c + fabsf((float)u * inv));
+            const double ey = (double)(c + fabsf((float)v * inv));
+            if (ex >= thx) {
+                if (!(h == lhx && u == lux)) {
+                    lhx = h;
+                    lux = u;
+                    lsx = exact_speed(g, (double)h, (double)u);
+                }
+                sx = fmax(sx, lsx);
+            }
+            if (ey >= thy) {
+                if (!(h == lhy && v == lvy)) {
+                    lhy = h;
+                    lvy = v;
+                    lsy = exact_speed(g, (double)h, (double)v);
+                }
+                sy = fmax(sy, lsy);
+            }
+        }
+    }
+    sx = block_reduce<false, true>(sx);
+    sy = block_reduce<false, true>(sy);
+    if (threadIdx.x == 0) {
+        scratch[3 * kRedBlocks + 8 + blockIdx.x] = sx;
+        scratch[4 * kRedBlocks + 8 + blockIdx.x] = sy;
+    }
+}
+
+__global__ void __launch_bounds__(1024) cfl_final_kernel(const double *scratch, int n, double dx, double dy,
+                                                         double cfl, double *out)
+{
+    double sx = 0.0, sy = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sx = fmax(sx, scratch[3 * kRedBlocks + 8 + i]);
+        sy = fmax(sy, scratch[4 * kRedBlocks + 8 + i]);
+    }
+    sx = block_reduce<false, true>(sx);
+    sy = block_reduce<false, true>(sy);
+    if (threadIdx.x == 0) {
+        const double tx = __ddiv_rn(dx, sx), ty = __ddiv_rn(dy, sy);
+        out[0] = __dmul_rn(cfl, fmin(tx, ty));
+        out[1] = scratch[3 * kRedBlocks + 2];
     }
 }
 
@@ -123,10 +249,21 @@ cudaError_t launch_mass(int dtype, const void *H, int nx, int ny, long long pitc
                         double *out_dev, cudaStream_t s)
 {
     const int nb = red_blocks(ny);
-    if (dtype == SWE_F64)
-        mass_partial_kernel<double><<<nb, kRedThreads, 0, s>>>(static_cast<const double *>(H), nx, ny, pitch, scratch);
-    else
-        mass_partial_kernel<float><<<nb, kRedThreads, 0, s>>>(static_cast<const float *>(H), nx, ny, pitch, scratch);
+    const size_t es = dtype == SWE_F64 ? 8 : 4;
+    const bool vec = ((uintptr_t)H % 16 == 0) && (((size_t)pitch * es) % 16 == 0);
+    if (dtype == SWE_F64) {
+        const double *h = static_cast<const double *>(H);
+        if (vec)
+            mass_partial_kernel<double, true><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
+        else
+            mass_partial_kernel<double, false><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
+    } else {
+        const float *h = static_cast<const float *>(H);
+        if (vec)
+            mass_partial_kernel<float, true><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
+        else
+            mass_partial_kernel<float, false><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
+    }
     sum_final_kernel<<<1, 1024, 0, s>>>(scratch, nb, dxdy, out_dev);
     return cudaGetLastError();
 }
@@ -135,18 +272,21 @@ cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, i
                        double dx, double dy, double g, double cfl, double *scratch, double *out_dev, cudaStream_t s)
 {
     const int nb = red_blocks(ny);
-    double *pmin = scratch, *pbad = scratch + kRedBlocks;
-    if (dtype == SWE_F64)
-        cfl_partial_kernel<double><<<nb, kRedThreads, 0, s>>>(static_cast<const double *>(H),
-                                                              static_cast<const double *>(U),
-                                                              static_cast<const double *>(V), nx, ny, pitch, dx, dy, g,
-                                                              pmin, pbad);
-    else
-        cfl_partial_kernel<float><<<nb, kRedThreads, 0, s>>>(static_cast<const float *>(H),
-                                                             static_cast<const float *>(U),
-                                                             static_cast<const float *>(V), nx, ny, pitch, dx, dy, g,
-                                                             pmin, pbad);
-    cfl_final_kernel<<<1, 1024, 0, s>>>(pmin, pbad, nb, cfl, out_dev);
+    const float g32 = (float)g;
+    if (dtype == SWE_F64) {
+        const double *h = static_cast<const double *>(H), *u = static_cast<const double *>(U),
+                     *v = static_cast<const double *>(V);
+        cfl_pass1_kernel<double><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, scratch);
+        cfl_pass1_final_kernel<<<1, 1024, 0, s>>>(scratch, nb);
+        cfl_pass2_kernel<double><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, g, scratch);
+    } else {
+        const float *h = static_cast<const float *>(H), *u = static_cast<const float *>(U),
+                    *v = static_cast<const float *>(V);
+        cfl_pass1_kernel<float><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, scratch);
+        cfl_pass1_final_kernel<<<1, 1024, 0, s>>>(scratch, nb);
+        cfl_pass2_kernel<float><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, g, scratch);
+    }
+    cfl_final_kernel<<<1, 1024, 0, s>>>(scratch, nb, dx, dy, cfl, out_dev);
     return cudaGetLastError();
 }
 

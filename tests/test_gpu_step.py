@@ -200,3 +200,32 @@ def test_full_size_8192_sampled_windows(dtype):
             assert err <= tol, (w, k, err)
     assert np.isfinite(hlast).all() and hlast.min() > 0
     assert abs(m1 - m0) / m0 <= (1e-13 if dtype == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("case", ["flat", "near_ties", "single_peak", "flow"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_cfl_exact_on_flat_and_near_tie_states(case, dtype):
+    """The CFL reduction screens cells with an FP32 estimate and evaluates
+    FP64 only near the maximum; the result must still equal the oracle's
+    exact FP64 minimum bitwise, including on plateaus and near-ties."""
+    from paper_1107_2157_gb300 import Grid
+    nx, ny, dx, dy = 333, 211, 0.9, 1.2
+    npd = np.float32 if dtype == "f32" else np.float64
+    rng = np.random.default_rng(7)
+    if case == "flat":
+        h = np.full((ny, nx), 1.25); hu = np.full((ny, nx), 0.1); hv = np.full((ny, nx), -0.2)
+    elif case == "near_ties":
+        h = 1.0 + 1e-7 * rng.standard_normal((ny, nx)); hu = 1e-7 * rng.standard_normal((ny, nx))
+        hv = np.zeros((ny, nx))
+    elif case == "single_peak":
+        h = np.full((ny, nx), 1.0); h[100, 200] = 1.0 + 1e-6; hu = np.zeros((ny, nx)); hv = np.zeros((ny, nx))
+        hv[3, 5] = 1e-6
+    else:
+        s = si.smooth_flow_state(99, nx, ny)
+        h, hu, hv = s.h, s.hu, s.hv
+    h, hu, hv = (np.ascontiguousarray(a.astype(npd)) for a in (h, hu, hv))
+    with Grid(nx, ny, dx, dy, 0.01, G, dtype=dtype) as grid:
+        grid.set_state(h, hu, hv)
+        dt = grid.cfl_dt(0.2)
+    ref = oracle.cfl_dt(h.astype(np.float64), hu.astype(np.float64), hv.astype(np.float64), dx, dy, G, 0.2)
+    assert dt == ref, (dt, ref)
