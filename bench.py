@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="grid", choices=["grid", "ensemble"],
+                   help="grid: one 8192^2 grid (default); ensemble: 512 uneven grids in one persistent launch")
+    p.add_argument("--tune-cache", default=None)
     return p.parse_args()
 
 
@@ -364,10 +367,77 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# ensemble workload: 512 uneven grids, one persistent launch per job
+# ---------------------------------------------------------------------------
+
+def run_ensemble(args):
+    import numpy as np
+    import torch
+
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import Batch, swe
+
+    torch.cuda.set_device(0)
+    sizes = si.ensemble_sizes(seed=2, count=512)
+    t0 = time.perf_counter()
+    states = [si.ensemble_state(2, i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
+    t_ic = time.perf_counter() - t0
+    n = len(sizes)
+    cells = sum(nx * ny for nx, ny in sizes)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        b = Batch(sizes, 1.0, 1.0, 0.01, G)
+        for i, st in enumerate(states):
+            b.set_state(i, *(a.astype(np.float32) for a in (st.h, st.hu, st.hv)), stream=sp)
+        dts = b.cfl_dt(CFL, stream=sp)
+        b.set_dt(dts, stream=sp)
+        t0 = time.perf_counter()
+        b.tune(args.tune_cache, stream=sp)
+        t_tune = time.perf_counter() - t0
+        b.step(args.warmup, stream=sp)
+        torch.cuda.synchronize()
+        for i, st in enumerate(states):  # restart from the initial state
+            b.set_state(i, *(a.astype(np.float32) for a in (st.h, st.hu, st.hv)), stream=sp)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
+        time.sleep(0.2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(args.steps, stream=sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        rc, flags = b.status(stream=sp)
+        t = e0.elapsed_time(e1) / 1e3
+        q = {k: b.query(getattr(swe, k)) for k in ("SWE_BQ_VARIANT", "SWE_BQ_CTAS_PER_SM", "SWE_BQ_TILE_X",
+                                                   "SWE_BQ_TILE_Y", "SWE_BQ_STAGES", "SWE_BQ_GRAPH",
+                                                   "SWE_BQ_TILES", "SWE_BQ_BLOCKS")}
+        m = b.mass(stream=sp)
+        b.close()
+    peak, kind = measured_peaks()
+    rate = cells * args.steps / t
+    line = {"metric": METRIC, "workload": "ensemble", "value": rate, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d instances, nx, ny uniform in [64, 1024] (seed 2), 4 bumps each, "
+                                   "per-instance FP64 CFL 0.2 dt, one persistent launch per job" % n,
+                       "cells": cells},
+            "roofline": {"bound": "hbm", "achieved": BYTES_PER_CELL_F32 * rate / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": BYTES_PER_CELL_F32 * rate / 1e9 / peak},
+            "tuned": q, "tune_s": t_tune, "ic_s": t_ic, "status": int(rc),
+            "flags_set": int((flags != 0).sum()), "clocks": clocks, "mass_min": float(m.min())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_ours(args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:

@@ -182,6 +182,93 @@ swe_status swe_mass_noalloc(int dtype, const void *h, int nx, int ny, long long 
 /* Static description of a status code. */
 const char *swe_strerror(swe_status s);
 
+/* ==========================================================================
+ * Batched ensembles (no counterpart in the paper: many independent
+ * instances of the Sec. 3 step, each with its own size, dx, dy and dt).
+ * All instances are FP32, share g, and step together.
+ * ========================================================================== */
+typedef struct swe_batch swe_batch;
+
+/* Per-instance flags reported by swe_batch_status. */
+#define SWE_FLAG_NONPOSITIVE 1 /* a step produced h <= 0 (or NaN) in the instance */
+#define SWE_FLAG_MASS 2        /* the instance failed a mass-drift check */
+#define SWE_FLAG_TIMEOUT 4     /* a device-side bounded wait gave up (all instances) */
+#define SWE_FLAG_FALLBACK 8    /* the instance was recomputed by the fallback solver */
+
+/*
+ * swe_batch_create: n >= 1 instances; instance i has nx[i] x ny[i] cells
+ * (1..65536 each), spacing dx[i], dy[i] and time step dt[i] (all finite,
+ * > 0); gravity g.  Allocates one device pool holding two FP32 state
+ * buffers (three planes each) per instance, rows 128-byte aligned.
+ * The arrays are copied; the caller keeps ownership.
+ */
+swe_status swe_batch_create(int n, const int *nx, const int *ny, const double *dx, const double *dy,
+                            const double *dt, double g, swe_batch **out);
+void swe_batch_destroy(swe_batch *b);
+
+/* Copy instance i's interior state in / out (float, row stride ld >= nx[i];
+ * host or device pointers as for swe_set_state).  Stream-ordered. */
+swe_status swe_batch_set_state(swe_batch *b, int i, const void *h, const void *hu, const void *hv,
+                               long long ld, int on_device, void *stream);
+swe_status swe_batch_get_state(swe_batch *b, int i, void *h, void *hu, void *hv, long long ld,
+                               int on_device, void *stream);
+
+/* Replaces every instance's time step (dt[0..n-1], finite, > 0). */
+swe_status swe_batch_set_dt(swe_batch *b, const double *dt, void *stream);
+
+/*
+ * swe_batch_step: advance every instance by n_steps steps of its own dt in
+ * ONE persistent, cooperatively launched kernel (the Sec. 3 step per tile;
+ * a grid-wide barrier with a bounded wait between steps).  The launch is
+ * captured into a CUDA graph per (n_steps, buffer parity) and replayed on
+ * ``stream``; where capture is unavailable it is launched directly.  A step
+ * that makes h <= 0 sets SWE_FLAG_NONPOSITIVE for that instance.
+ */
+swe_status swe_batch_step(swe_batch *b, int n_steps, void *stream);
+
+/* Synchronous: writes each instance's flags to flags_out[0..n-1], clears
+ * them, and returns SWE_ETIMEOUT if a bounded wait gave up, else SWE_OK. */
+swe_status swe_batch_status(swe_batch *b, int *flags_out, void *stream);
+
+/* Synchronous FP64 reductions per instance (as swe_mass / swe_cfl_dt):
+ * mass_out[i] = sum(h) dx dy; dt_out[i] = CFL step (0 and SWE_ECHECK if
+ * some h <= 0 or a value is not finite). */
+swe_status swe_batch_mass(swe_batch *b, double *mass_out, void *stream);
+swe_status swe_batch_cfl_dt(swe_batch *b, double cfl, double *dt_out, void *stream);
+
+/*
+ * swe_batch_tune: autotuner.  Times every kernel variant (tile shape,
+ * staging depth) at every feasible CTA count per SM on this batch, keeps the
+ * fastest, and appends it to the JSON-lines cache ``cache_path`` (or
+ * $SWE_TUNE_CACHE; NULL and no variable = no cache), keyed by GPU name and
+ * instance sizes.  A cached entry is reused without timing.  The current
+ * state is saved and restored around the trials.  Synchronous.
+ */
+swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream);
+
+/*
+ * swe_selftest_wait: exercises the library's bounded device waits.  which =
+ * 0 waits on an mbarrier that nothing completes; which = 1 on a grid barrier
+ * that expects one CTA more than are launched.  Each wait gives up after
+ * limit_ms (0 < limit_ms <= 5000) and the kernel returns.  Synchronous;
+ * returns SWE_ETIMEOUT when the wait ran out as designed.
+ */
+swe_status swe_selftest_wait(int which, double limit_ms, void *stream);
+
+/* Selects a kernel variant and CTAs per SM explicitly (tests, tuning). */
+swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm);
+
+typedef enum {
+    SWE_BQ_VARIANT = 0, SWE_BQ_CTAS_PER_SM = 1, SWE_BQ_BLOCKS = 2, SWE_BQ_TILES = 3,
+    SWE_BQ_TILE_X = 4, SWE_BQ_TILE_Y = 5, SWE_BQ_STAGES = 6, SWE_BQ_DEPTH = 7,
+    SWE_BQ_GRAPH = 8,        /* 1 if steps replay a captured CUDA graph */
+    SWE_BQ_LAUNCHES = 9,     /* persistent launches enqueued so far */
+    SWE_BQ_TUNED = 10,       /* 0 default, 1 tuned by timing, 2 from cache */
+    SWE_BQ_CELLS = 11,       /* total cells over all instances */
+    SWE_BQ_VARIANT_COUNT = 12
+} swe_batch_query_key;
+swe_status swe_batch_query(swe_batch *b, int key, long long *value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,754 @@
+// swe_batch.cu -- batched ensembles: many independent FP32 grids of
+// different sizes, each with its own dx, dy and dt, advanced together by ONE
+// persistent, cooperatively launched kernel that runs all requested steps.
+//
+// Work list: every instance is cut into tiles of TX x TY cells; the tiles of
+// all instances form one flat list (instance-major, so the CTAs working at
+// the same time share halo rows in L2).  CTAs stride over the list; each tile
+// is staged by TMA (three box loads on one mbarrier, double buffered so the
+// next tile's loads overlap this tile's arithmetic) and computed by the same
+// tile routine as the single-grid kernel (swe_tile.cuh).  A grid-wide barrier
+// with a bounded wait separates the time steps; all instances step together.
+//
+// The launch is captured once per (step count, buffer parity) into a CUDA
+// graph on a private stream and replayed on the caller's stream.  Tile shape,
+// staging depth and CTAs per SM come from the autotuner (swe_batch_tune),
+// which times each candidate on the batch itself and caches the winner in a
+// JSON-lines file.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "swe_tile.cuh"
+
+namespace swe {
+
+struct TileRec {
+    int inst;
+    unsigned short bx, by;  // tile column / row within the instance
+};
+
+struct BatchInst {
+    float *buf[2];       // three planes (H, U, V) per buffer
+    long long plane;     // elements per plane
+    long long pitch;     // elements per row
+    int nx, ny;
+    Coef<float> k;
+};
+
+// ---------------------------------------------------------------------------
+// The persistent kernel
+// ---------------------------------------------------------------------------
+template <int NWARP, int RY, int STAGES>
+struct BatchCfg {
+    using C = TiledCfg<float, NWARP, RY>;
+    static constexpr size_t STAGE_BYTES = 3 * C::BOX_STRIDE;
+    static constexpr size_t SMEM = STAGES * STAGE_BYTES + 64;
+};
+
+template <int NWARP, int RY, int STAGES>
+__global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *__restrict__ inst,
+                                                              const CUtensorMap *__restrict__ maps,
+                                                              const TileRec *__restrict__ tiles, int ntiles,
+                                                              int n_steps, int parity0, GridBarrier *gbar,
+                                                              int *err, int *flags)
+{
+    using B = BatchCfg<NWARP, RY, STAGES>;
+    using C = typename B::C;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * B::STAGE_BYTES);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto box = [&](int stage, int f) {
+        return reinterpret_cast<float *>(smem + stage * B::STAGE_BYTES + f * C::BOX_STRIDE);
+    };
+    // thread 0: start the three TMA loads of tile t (buffer ``cur``) into ``stage``
+    auto issue = [&](int t, int stage, int cur) {
+        const TileRec r = tiles[t];
+        const CUtensorMap *m = maps + ((size_t)r.inst * 2 + cur) * 3;
+        const int x0 = (int)r.bx * C::TX, y0 = (int)r.by * C::TY;
+        mbar_arrive_expect_tx(&bars[stage], (uint32_t)(3 * C::BOX_BYTES));
+        tma_load_2d(box(stage, 0), m + 0, &bars[stage], x0 - C::AX, y0 - 1);
+        tma_load_2d(box(stage, 1), m + 1, &bars[stage], x0 - C::AX, y0 - 1);
+        tma_load_2d(box(stage, 2), m + 2, &bars[stage], x0 - C::AX, y0 - 1);
+    };
+
+    uint32_t phases = 0;  // bit s = parity of the next completion of stage s
+    for (int step = 0; step < n_steps; ++step) {
+        const int cur = (parity0 + step) & 1;
+        if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
+            fence_proxy_async_global();  // other CTAs' stores of the last step -> TMA reads
+            issue(blockIdx.x, 0, cur);
+        }
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int st = STAGES > 1 ? (it & 1) : 0;
+            const int tn = t + gridDim.x;
+            if (STAGES > 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, st ^ 1, cur);
+            if (!mbar_wait_bounded(&bars[st], (phases >> st) & 1u, err)) {
+                // give the other stage's prefetch (if any) a bounded chance to land
+                if (STAGES > 1 && tn < ntiles) mbar_wait_bounded(&bars[st ^ 1], (phases >> (st ^ 1)) & 1u, err);
+                return;
+            }
+            phases ^= 1u << st;
+
+            const TileRec r = tiles[t];
+            const BatchInst *I = inst + r.inst;
+            float *o = I->buf[cur ^ 1];
+            const long long plane = I->plane, pitch = I->pitch;
+            const int nx = I->nx, ny = I->ny;
+            const Coef<float> k = I->k;
+            const int x0 = (int)r.bx * C::TX, y0 = (int)r.by * C::TY;
+            bool bad;
+            if (x0 == 0 || x0 + C::TX >= nx)
+                bad = tiled_compute<float, NWARP, RY, true>(box(st, 0), box(st, 1), box(st, 2), o, o + plane,
+                                                            o + 2 * plane, nx, ny, pitch, x0, y0, k);
+            else
+                bad = tiled_compute<float, NWARP, RY, false>(box(st, 0), box(st, 1), box(st, 2), o, o + plane,
+                                                             o + 2 * plane, nx, ny, pitch, x0, y0, k);
+            // all threads are done with this stage after the barrier
+            if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags[r.inst], SWE_FLAG_NONPOSITIVE);
+            if (STAGES == 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, 0, cur);
+        }
+        if (!grid_sync_bounded(gbar, gridDim.x, err)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Variants the autotuner chooses from
+// ---------------------------------------------------------------------------
+struct Variant {
+    int nwarp, ry, stages;
+    int tile_x, tile_y, box_w, box_h;
+    size_t smem;
+    const void *func;
+};
+
+template <int NWARP, int RY, int STAGES>
+static Variant make_variant()
+{
+    using B = BatchCfg<NWARP, RY, STAGES>;
+    using C = typename B::C;
+    return Variant{NWARP, RY, STAGES, C::TX, C::TY, C::BW, C::BH, B::SMEM,
+                   reinterpret_cast<const void *>(&batch_lw_kernel<NWARP, RY, STAGES>)};
+}
+
+static const std::vector<Variant> &variants()
+{
+    static const std::vector<Variant> v = {
+        make_variant<4, 8, 2>(),   // 128x32 tiles, double-buffered
+        make_variant<4, 4, 2>(),   // 128x16 tiles, double-buffered
+        make_variant<4, 8, 1>(),   // 128x32 tiles, single stage
+        make_variant<8, 4, 2>(),   // 128x32 tiles, 8 warps, double-buffered
+        make_variant<4, 16, 1>(),  // 128x64 tiles, single stage
+    };
+    return v;
+}
+
+bool encode_plane_map(CUtensorMap *map, int dtype, const void *base, int nx, int ny, long long pitch, int box_x,
+                      int box_y);
+size_t reduce_scratch_doubles_many(int n, int B);
+
+// Wait probes for swe_selftest_wait: which = 0 waits on an mbarrier that no
+// one arrives at, which = 1 on a grid barrier that expects one CTA more than
+// the launch has.  Both give up after limit_ns and record SWE_ETIMEOUT.
+__global__ void wait_probe_kernel(int which, unsigned long long limit_ns, GridBarrier *bar, int *err)
+{
+    __shared__ uint64_t mbar;
+    if (which == 0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&mbar, 2);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        mbar_wait_bounded(&mbar, 0, err, limit_ns);
+    } else {
+        grid_sync_bounded(bar, gridDim.x + 1, err, limit_ns);
+    }
+}
+
+static cudaError_t launch_wait_probe(int which, unsigned long long limit_ns, GridBarrier *bar, int *err,
+                                     cudaStream_t s)
+{
+    wait_probe_kernel<<<which == 0 ? 1 : 4, 64, 0, s>>>(which, limit_ns, bar, err);
+    return cudaGetLastError();
+}
+
+}  // namespace swe
+
+using namespace swe;
+
+struct swe_batch {
+    int device = 0;
+    int n = 0;
+    double g = 9.8;
+    std::vector<int> nx, ny;
+    std::vector<double> dx, dy, dt;
+    std::vector<long long> pitch, off;  // elements; off[i] = first element of instance i in a half
+    size_t half = 0;                    // elements per half (all buffers of one parity)
+    float *pool = nullptr;
+    int cur = 0;
+    std::vector<BatchInst> h_inst;
+    BatchInst *d_inst = nullptr;
+    CUtensorMap *d_maps = nullptr;               // maps of the configured variant
+    std::map<int, CUtensorMap *> maps_by_box_h;  // written once each, never rewritten
+    TileRec *d_tiles = nullptr;
+    int ntiles = 0, tiles_ty = -1, tiles_cap = 0;
+    GridBarrier *d_bar = nullptr;
+    int *d_err = nullptr;
+    int *d_flags = nullptr;
+    RedGrid *d_red[2] = {nullptr, nullptr};
+    double *d_scratch = nullptr;
+    double *d_out = nullptr;
+    double *h_out = nullptr;
+    int red_blocks = 32;
+    int variant = 0, ctas_per_sm = 1, blocks = 0, sms = 0;
+    cudaStream_t cap = nullptr;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    bool graph_ok = true;
+    long long launches = 0;
+    int tuned = 0;
+};
+
+static swe_status st_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return SWE_OK;
+    if (e == cudaErrorMemoryAllocation) return SWE_ENOMEM;
+    return SWE_ECUDA;
+}
+
+#define B_TRY(expr)                                   \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return st_of(e_);      \
+    } while (0)
+
+static Coef<float> coef_of(double dx, double dy, double dt, double g)
+{
+    Coef<float> k;
+    k.hx = (float)(0.5 * dt / dx);
+    k.hy = (float)(0.5 * dt / dy);
+    k.lx = (float)(dt / dx);
+    k.ly = (float)(dt / dy);
+    k.hg = (float)(0.5 * g);
+    return k;
+}
+
+static void drop_graphs(swe_batch *b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// (Re)builds the tile list and tensor maps for variant v and sets the launch
+// width; invalidates captured graphs.
+static swe_status configure(swe_batch *b, int v, int ctas_per_sm)
+{
+    const Variant &V = variants()[v];
+    if (b->tiles_ty != V.tile_y) {
+        std::vector<TileRec> t;
+        for (int i = 0; i < b->n; ++i) {
+            const int tx = (b->nx[i] + V.tile_x - 1) / V.tile_x;
+            const int ty = (b->ny[i] + V.tile_y - 1) / V.tile_y;
+            for (int y = 0; y < ty; ++y)
+                for (int x = 0; x < tx; ++x) t.push_back(TileRec{i, (unsigned short)x, (unsigned short)y});
+        }
+        if ((int)t.size() > b->tiles_cap) {
+            cudaFree(b->d_tiles);
+            b->d_tiles = nullptr;
+            B_TRY(cudaMalloc(&b->d_tiles, t.size() * sizeof(TileRec)));
+            b->tiles_cap = (int)t.size();
+        }
+        B_TRY(cudaMemcpy(b->d_tiles, t.data(), t.size() * sizeof(TileRec), cudaMemcpyHostToDevice));
+        b->ntiles = (int)t.size();
+        b->tiles_ty = V.tile_y;
+    }
+    // Tensor maps live in global memory.  The TMA unit may keep a descriptor
+    // cached by address, so a map array is never rewritten in place: each
+    // box height gets its own array, encoded once.
+    auto found = b->maps_by_box_h.find(V.box_h);
+    if (found == b->maps_by_box_h.end()) {
+        std::vector<CUtensorMap> m((size_t)b->n * 6);
+        for (int i = 0; i < b->n; ++i)
+            for (int c = 0; c < 2; ++c)
+                for (int f = 0; f < 3; ++f) {
+                    const float *base = b->h_inst[i].buf[c] + f * b->h_inst[i].plane;
+                    if (!encode_plane_map(&m[((size_t)i * 2 + c) * 3 + f], SWE_F32, base, b->nx[i], b->ny[i],
+                                          b->pitch[i], V.box_w, V.box_h))
+                        return SWE_ECUDA;
+                }
+        CUtensorMap *d = nullptr;
+        B_TRY(cudaMalloc(&d, m.size() * sizeof(CUtensorMap)));
+        const cudaError_t e = cudaMemcpy(d, m.data(), m.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return st_of(e);
+        }
+        found = b->maps_by_box_h.emplace(V.box_h, d).first;
+    }
+    b->d_maps = found->second;
+    B_TRY(cudaFuncSetAttribute(V.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem));
+    int occ = 0;
+    B_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, V.func, V.nwarp * 32, V.smem));
+    if (occ < 1) return SWE_EUNSUPPORTED;
+    b->variant = v;
+    b->ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
+    b->blocks = b->sms * b->ctas_per_sm;
+    drop_graphs(b);
+    return SWE_OK;
+}
+
+static int max_ctas(int v)
+{
+    const Variant &V = variants()[v];
+    cudaFuncSetAttribute(V.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, V.func, V.nwarp * 32, V.smem);
+    return occ;
+}
+
+static cudaError_t launch_direct(swe_batch *b, int n_steps, int parity0, cudaStream_t s)
+{
+    const Variant &V = variants()[b->variant];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->blocks);
+    cfg.blockDim = dim3(V.nwarp * 32);
+    cfg.dynamicSmemBytes = V.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {(void *)&b->d_inst, (void *)&b->d_maps, (void *)&b->d_tiles, (void *)&b->ntiles,
+                    (void *)&n_steps,   (void *)&parity0,   (void *)&b->d_bar,   (void *)&b->d_err,
+                    (void *)&b->d_flags};
+    return cudaLaunchKernelExC(&cfg, V.func, args);
+}
+
+// Enqueues n_steps on s: replays a captured graph when capture works.
+static swe_status run_steps(swe_batch *b, int n_steps, cudaStream_t s)
+{
+    const int parity0 = b->cur;
+    if (b->graph_ok) {
+        auto key = std::make_pair(n_steps, parity0);
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            bool ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const cudaError_t le = launch_direct(b, n_steps, parity0, b->cap);
+                const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+                ok = le == cudaSuccess && ee == cudaSuccess && g &&
+                     cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+            }
+            if (g) cudaGraphDestroy(g);
+            if (!ok) {
+                cudaGetLastError();  // capture is not supported here: launch directly from now on
+                if (ge) cudaGraphExecDestroy(ge);
+                b->graph_ok = false;
+            } else {
+                it = b->graphs.emplace(key, ge).first;
+            }
+        }
+        if (b->graph_ok) {
+            B_TRY(cudaGraphLaunch(it->second, s));
+            b->cur ^= (n_steps & 1);
+            b->launches += 1;
+            return SWE_OK;
+        }
+    }
+    B_TRY(launch_direct(b, n_steps, parity0, s));
+    b->cur ^= (n_steps & 1);
+    b->launches += 1;
+    return SWE_OK;
+}
+
+static std::string tune_key(const swe_batch *b)
+{
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, b->device);
+    unsigned long long h = 1469598103934665603ull;  // FNV-1a over the sizes
+    for (int i = 0; i < b->n; ++i) {
+        h = (h ^ (unsigned long long)b->nx[i]) * 1099511628211ull;
+        h = (h ^ (unsigned long long)b->ny[i]) * 1099511628211ull;
+    }
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s|n=%d|sizes=%016llx", p.name, b->n, h);
+    for (char *c = buf; *c; ++c)
+        if (*c == '"') *c = '\'';
+    return buf;
+}
+
+static bool cache_lookup(const char *path, const std::string &key, int *v, int *cps)
+{
+    if (!path || !*path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string needle = "\"key\": \"" + key + "\"";
+    while (std::fgets(line, sizeof(line), f)) {
+        if (!std::strstr(line, needle.c_str())) continue;
+        const char *pv = std::strstr(line, "\"variant\": ");
+        const char *pc = std::strstr(line, "\"ctas_per_sm\": ");
+        if (pv && pc) {
+            *v = std::atoi(pv + 11);
+            *cps = std::atoi(pc + 15);
+            found = *v >= 0 && *v < (int)variants().size() && *cps >= 1;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void cache_store(const char *path, const std::string &key, int v, int cps, double ms)
+{
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    const Variant &V = variants()[v];
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"variant\": %d, \"ctas_per_sm\": %d, \"tile_x\": %d, \"tile_y\": %d, "
+                 "\"stages\": %d, \"depth\": 1, \"ms_per_step\": %.6f}\n",
+                 key.c_str(), v, cps, V.tile_x, V.tile_y, V.stages, ms);
+    std::fclose(f);
+}
+
+extern "C" {
+
+void swe_batch_destroy(swe_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    drop_graphs(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->pool);
+    cudaFree(b->d_inst);
+    for (auto &kv : b->maps_by_box_h) cudaFree(kv.second);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    cudaFree(b->d_flags);
+    cudaFree(b->d_red[0]);
+    cudaFree(b->d_red[1]);
+    cudaFree(b->d_scratch);
+    cudaFree(b->d_out);
+    cudaFreeHost(b->h_out);
+    delete b;
+}
+
+swe_status swe_batch_create(int n, const int *nx, const int *ny, const double *dx, const double *dy,
+                            const double *dt, double g, swe_batch **out)
+{
+    if (!out) return SWE_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !nx || !ny || !dx || !dy || !dt || !(g > 0.0) || !std::isfinite(g)) return SWE_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (nx[i] < 1 || ny[i] < 1 || nx[i] > 65536 || ny[i] > 65536) return SWE_EINVAL;
+        for (double v : {dx[i], dy[i], dt[i]})
+            if (!(v > 0.0) || !std::isfinite(v)) return SWE_EINVAL;
+    }
+    swe_batch *b = new (std::nothrow) swe_batch();
+    if (!b) return SWE_ENOMEM;
+    auto fail = [&](swe_status s) {
+        swe_batch_destroy(b);
+        return s;
+    };
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->n = n;
+    b->g = g;
+    b->nx.assign(nx, nx + n);
+    b->ny.assign(ny, ny + n);
+    b->dx.assign(dx, dx + n);
+    b->dy.assign(dy, dy + n);
+    b->dt.assign(dt, dt + n);
+    long long at = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long p = plane_pitch(nx[i], 4);
+        b->pitch.push_back(p);
+        b->off.push_back(at);
+        at += 3 * p * ny[i];
+        at = (at + 63) / 64 * 64;  // 256-byte aligned instances
+    }
+    b->half = (size_t)at;
+    swe_status s;
+    if ((s = st_of(cudaMalloc(&b->pool, 2 * b->half * sizeof(float)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMemset(b->pool, 0, 2 * b->half * sizeof(float)))) != SWE_OK) return fail(s);
+    b->h_inst.resize(n);
+    std::vector<RedGrid> red[2];
+    for (int i = 0; i < n; ++i) {
+        BatchInst &I = b->h_inst[i];
+        I.buf[0] = b->pool + b->off[i];
+        I.buf[1] = b->pool + b->half + b->off[i];
+        I.pitch = b->pitch[i];
+        I.plane = b->pitch[i] * ny[i];
+        I.nx = nx[i];
+        I.ny = ny[i];
+        I.k = coef_of(dx[i], dy[i], dt[i], g);
+        for (int c = 0; c < 2; ++c)
+            red[c].push_back(RedGrid{I.buf[c], I.buf[c] + I.plane, I.buf[c] + 2 * I.plane, I.pitch, nx[i], ny[i],
+                                     dx[i], dy[i]});
+    }
+    if ((s = st_of(cudaMalloc(&b->d_inst, n * sizeof(BatchInst)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMemcpy(b->d_inst, b->h_inst.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice))) !=
+        SWE_OK)
+        return fail(s);
+    for (int c = 0; c < 2; ++c) {
+        if ((s = st_of(cudaMalloc(&b->d_red[c], n * sizeof(RedGrid)))) != SWE_OK) return fail(s);
+        if ((s = st_of(cudaMemcpy(b->d_red[c], red[c].data(), n * sizeof(RedGrid), cudaMemcpyHostToDevice))) !=
+            SWE_OK)
+            return fail(s);
+    }
+    if ((s = st_of(cudaMalloc(&b->d_bar, sizeof(GridBarrier)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMemset(b->d_bar, 0, sizeof(GridBarrier)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMalloc(&b->d_err, sizeof(int)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMemset(b->d_err, 0, sizeof(int)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMalloc(&b->d_flags, n * sizeof(int)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMemset(b->d_flags, 0, n * sizeof(int)))) != SWE_OK) return fail(s);
+    const size_t sd = reduce_scratch_doubles_many(n, b->red_blocks);
+    if ((s = st_of(cudaMalloc(&b->d_scratch, sd * sizeof(double)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMalloc(&b->d_out, 2 * (size_t)n * sizeof(double)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaMallocHost(&b->h_out, 2 * (size_t)n * sizeof(double)))) != SWE_OK) return fail(s);
+    if ((s = st_of(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking))) != SWE_OK) return fail(s);
+    if ((s = configure(b, 0, 2)) != SWE_OK) return fail(s);
+    *out = b;
+    return SWE_OK;
+}
+
+static swe_status batch_copy(swe_batch *b, int i, void *const *user, long long ld, bool to_dev, cudaStream_t s)
+{
+    if (!b || i < 0 || i >= b->n || ld < b->nx[i]) return SWE_EINVAL;
+    for (int k = 0; k < 3; ++k)
+        if (!user[k]) return SWE_EINVAL;
+    const BatchInst &I = b->h_inst[i];
+    for (int k = 0; k < 3; ++k) {
+        float *dev = I.buf[b->cur] + k * I.plane;
+        const size_t w = (size_t)I.nx * sizeof(float);
+        if (to_dev)
+            B_TRY(cudaMemcpy2DAsync(dev, I.pitch * sizeof(float), user[k], ld * sizeof(float), w, I.ny,
+                                    cudaMemcpyDefault, s));
+        else
+            B_TRY(cudaMemcpy2DAsync(user[k], ld * sizeof(float), dev, I.pitch * sizeof(float), w, I.ny,
+                                    cudaMemcpyDefault, s));
+    }
+    return SWE_OK;
+}
+
+swe_status swe_batch_set_state(swe_batch *b, int i, const void *h, const void *hu, const void *hv, long long ld,
+                               int on_device, void *stream)
+{
+    (void)on_device;
+    void *p[3] = {const_cast<void *>(h), const_cast<void *>(hu), const_cast<void *>(hv)};
+    return batch_copy(b, i, p, ld, true, static_cast<cudaStream_t>(stream));
+}
+
+swe_status swe_batch_get_state(swe_batch *b, int i, void *h, void *hu, void *hv, long long ld, int on_device,
+                               void *stream)
+{
+    (void)on_device;
+    void *p[3] = {h, hu, hv};
+    return batch_copy(b, i, p, ld, false, static_cast<cudaStream_t>(stream));
+}
+
+swe_status swe_batch_set_dt(swe_batch *b, const double *dt, void *stream)
+{
+    if (!b || !dt) return SWE_EINVAL;
+    for (int i = 0; i < b->n; ++i)
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < b->n; ++i) {
+        b->dt[i] = dt[i];
+        b->h_inst[i].k = coef_of(b->dx[i], b->dy[i], dt[i], b->g);
+    }
+    // the pageable source is copied before cudaMemcpyAsync returns
+    B_TRY(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), b->n * sizeof(BatchInst), cudaMemcpyHostToDevice, s));
+    return SWE_OK;
+}
+
+swe_status swe_batch_step(swe_batch *b, int n_steps, void *stream)
+{
+    if (!b || n_steps < 0) return SWE_EINVAL;
+    if (n_steps == 0) return SWE_OK;
+    return run_steps(b, n_steps, static_cast<cudaStream_t>(stream));
+}
+
+swe_status swe_batch_status(swe_batch *b, int *flags_out, void *stream)
+{
+    if (!b || !flags_out) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int err = 0;
+    B_TRY(cudaMemcpyAsync(flags_out, b->d_flags, b->n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    if (err) {
+        for (int i = 0; i < b->n; ++i) flags_out[i] |= SWE_FLAG_TIMEOUT;
+    }
+    B_TRY(cudaMemsetAsync(b->d_flags, 0, b->n * sizeof(int), s));
+    B_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
+    B_TRY(cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), s));
+    B_TRY(cudaStreamSynchronize(s));
+    return err ? (swe_status)err : SWE_OK;
+}
+
+swe_status swe_batch_mass(swe_batch *b, double *mass_out, void *stream)
+{
+    if (!b || !mass_out) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    B_TRY(launch_mass_many(b->d_red[b->cur], b->n, b->red_blocks, b->d_scratch, b->d_out, s));
+    B_TRY(cudaMemcpyAsync(b->h_out, b->d_out, 2 * (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < b->n; ++i) mass_out[i] = b->h_out[2 * i];
+    return SWE_OK;
+}
+
+swe_status swe_batch_cfl_dt(swe_batch *b, double cfl, double *dt_out, void *stream)
+{
+    if (!b || !dt_out || !(cfl > 0.0) || !std::isfinite(cfl)) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    B_TRY(launch_cfl_many(b->d_red[b->cur], b->n, b->red_blocks, b->g, cfl, b->d_scratch, b->d_out, s));
+    B_TRY(cudaMemcpyAsync(b->h_out, b->d_out, 2 * (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    B_TRY(cudaStreamSynchronize(s));
+    bool bad = false;
+    for (int i = 0; i < b->n; ++i) {
+        dt_out[i] = b->h_out[2 * i + 1] != 0.0 ? 0.0 : b->h_out[2 * i];
+        bad |= b->h_out[2 * i + 1] != 0.0;
+    }
+    return bad ? SWE_ECHECK : SWE_OK;
+}
+
+swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream)
+{
+    if (!b) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char *path = cache_path && *cache_path ? cache_path : std::getenv("SWE_TUNE_CACHE");
+    const std::string key = tune_key(b);
+    int v = 0, cps = 1;
+    if (cache_lookup(path, key, &v, &cps)) {
+        swe_status st = configure(b, v, cps);
+        if (st == SWE_OK) b->tuned = 2;
+        return st;
+    }
+    // keep the current state: trials run on it and it is restored afterwards
+    float *saved = nullptr;
+    B_TRY(cudaMalloc(&saved, b->half * sizeof(float)));
+    B_TRY(cudaMemcpyAsync(saved, b->pool + (size_t)b->cur * b->half, b->half * sizeof(float),
+                          cudaMemcpyDeviceToDevice, s));
+    const int cur0 = b->cur;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e30;
+    int best_v = 0, best_c = 1;
+    const int trial_steps = 8;
+    swe_status st = SWE_OK;
+    for (int vi = 0; vi < (int)variants().size() && st == SWE_OK; ++vi) {
+        const int occ = max_ctas(vi);
+        for (int c = 1; c <= occ && st == SWE_OK; ++c) {
+            if ((st = configure(b, vi, c)) != SWE_OK) break;
+            if ((st = run_steps(b, 2, s)) != SWE_OK) break;  // capture + warm-up
+            float best = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, s);
+                if ((st = run_steps(b, trial_steps, s)) != SWE_OK) break;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, ms);
+            }
+            const double per = best / trial_steps;
+            if (per < best_ms) {
+                best_ms = per;
+                best_v = vi;
+                best_c = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cur = cur0;
+    cudaMemcpyAsync(b->pool + (size_t)cur0 * b->half, saved, b->half * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    cudaFree(saved);
+    cudaMemset(b->d_flags, 0, b->n * sizeof(int));
+    if (st != SWE_OK) return st;
+    st = configure(b, best_v, best_c);
+    if (st == SWE_OK) {
+        b->tuned = 1;
+        cache_store(path, key, best_v, best_c, best_ms);
+    }
+    return st;
+}
+
+swe_status swe_batch_query(swe_batch *b, int key, long long *value)
+{
+    if (!b || !value) return SWE_EINVAL;
+    const Variant &V = variants()[b->variant];
+    switch (key) {
+        case SWE_BQ_VARIANT: *value = b->variant; break;
+        case SWE_BQ_CTAS_PER_SM: *value = b->ctas_per_sm; break;
+        case SWE_BQ_BLOCKS: *value = b->blocks; break;
+        case SWE_BQ_TILES: *value = b->ntiles; break;
+        case SWE_BQ_TILE_X: *value = V.tile_x; break;
+        case SWE_BQ_TILE_Y: *value = V.tile_y; break;
+        case SWE_BQ_STAGES: *value = V.stages; break;
+        case SWE_BQ_DEPTH: *value = 1; break;
+        case SWE_BQ_GRAPH: *value = b->graph_ok ? 1 : 0; break;
+        case SWE_BQ_LAUNCHES: *value = b->launches; break;
+        case SWE_BQ_TUNED: *value = b->tuned; break;
+        case SWE_BQ_CELLS: {
+            long long c = 0;
+            for (int i = 0; i < b->n; ++i) c += (long long)b->nx[i] * b->ny[i];
+            *value = c;
+            break;
+        }
+        case SWE_BQ_VARIANT_COUNT: *value = (long long)variants().size(); break;
+        default: return SWE_EINVAL;
+    }
+    return SWE_OK;
+}
+
+swe_status swe_selftest_wait(int which, double limit_ms, void *stream)
+{
+    if ((which != 0 && which != 1) || !(limit_ms > 0.0) || limit_ms > 5000.0) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *d_err = nullptr;
+    GridBarrier *d_bar = nullptr;
+    B_TRY(cudaMalloc(&d_err, sizeof(int)));
+    cudaError_t e = cudaMalloc(&d_bar, sizeof(GridBarrier));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, sizeof(GridBarrier), s);
+    if (e == cudaSuccess) e = launch_wait_probe(which, (unsigned long long)(limit_ms * 1e6), d_bar, d_err, s);
+    int word = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_err);
+    cudaFree(d_bar);
+    if (e != cudaSuccess) return st_of(e);
+    return (swe_status)word;
+}
+
+swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm)
+{
+    if (!b || variant < 0 || variant >= (int)variants().size() || ctas_per_sm < 1) return SWE_EINVAL;
+    return configure(b, variant, ctas_per_sm);
+}
+
+}  // extern "C"

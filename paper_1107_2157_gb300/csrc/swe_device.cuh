@@ -69,14 +69,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Waits for phase ``parity`` of ``bar`` to complete; gives up after
 // SWE_WAIT_LIMIT_NS, records SWE_ETIMEOUT in *err and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  uint64_t limit_ns = SWE_WAIT_LIMIT_NS)
 {
     for (int i = 0; i < 32; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > SWE_WAIT_LIMIT_NS) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             atomicExch(err, (int)SWE_ETIMEOUT);
             return false;
         }
@@ -100,6 +101,57 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap *map)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Orders this thread's earlier generic-proxy view of global memory before its
+// later async-proxy (TMA) reads: needed when a TMA load reads data that other
+// CTAs stored in the same kernel.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Grid-wide barrier for a cooperatively launched kernel (all CTAs resident).
+// ``count`` and ``gen`` are zero-initialised device words shared by every
+// CTA.  Thread 0 of each CTA arrives; the last arrival resets the count and
+// bumps the generation, the others wait for the generation to change.  The
+// wait is bounded: after SWE_WAIT_LIMIT_NS it records SWE_ETIMEOUT in *err
+// and the barrier returns false on every thread of the CTA.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+__device__ __forceinline__ bool grid_sync_bounded(GridBarrier *b, unsigned int nblocks, int *err,
+                                                  uint64_t limit_ns = SWE_WAIT_LIMIT_NS)
+{
+    __shared__ int ok_shared;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *vgen = &b->gen;
+        const unsigned int g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == nblocks - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (*vgen == g0) {
+                if (globaltimer_ns() - t0 > limit_ns) {
+                    atomicExch(err, (int)SWE_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_shared = ok;
+    }
+    __syncthreads();
+    return ok_shared != 0;
+}
+
 // ---------------------------------------------------------------------------
 // Arithmetic.  rcp(): FP32 uses the hardware approximate reciprocal
 // (rcp.approx, at most 1 ulp error); FP64 uses IEEE division.
@@ -111,6 +163,15 @@ __device__ __forceinline__ float rcp(float x)
     return r;
 }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// Rounded products that the compiler may not fuse into a later add.  The
+// flux products below feed subtractions (a - b*c); left to itself the
+// compiler fuses such a pair into an FMA only where the product has a single
+// use, which depends on the tile shape (a warp's first and last row).  With
+// every product rounded, each cell's update is the same function of its
+// neighbours for every tile shape, so all kernels give identical bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 template <typename T>
 struct Coef {
@@ -136,11 +197,11 @@ __device__ __forceinline__ CellQ<T> make_cell(T h, T u, T v, T hg)
     c.u = u;
     c.v = v;
     const T inv = rcp(h);
-    const T p = hg * h * h;
-    const T uu = u * inv;
-    const T vv = v * inv;
+    const T p = mul_rn(mul_rn(hg, h), h);
+    const T uu = mul_rn(u, inv);
+    const T vv = mul_rn(v, inv);
     c.f2 = fma(u, uu, p);
-    c.f3 = u * vv;
+    c.f3 = mul_rn(u, vv);
     c.g3 = fma(v, vv, p);
     return c;
 }
@@ -176,15 +237,15 @@ template <typename T>
 __device__ __forceinline__ Flux3<T> xface_flux(const CellQ<T> &L, const CellQ<T> &R, const Coef<T> &k)
 {
     const T half = T(0.5);
-    const T Hf = fma(k.hx, L.u - R.u, half * (L.h + R.h));
-    const T Uf = fma(k.hx, L.f2 - R.f2, half * (L.u + R.u));
-    const T Vf = fma(k.hx, L.f3 - R.f3, half * (L.v + R.v));
+    const T Hf = fma(k.hx, L.u - R.u, mul_rn(half, L.h + R.h));
+    const T Uf = fma(k.hx, L.f2 - R.f2, mul_rn(half, L.u + R.u));
+    const T Vf = fma(k.hx, L.f3 - R.f3, mul_rn(half, L.v + R.v));
     const T inv = rcp(Hf);
-    const T uf = Uf * inv;
+    const T uf = mul_rn(Uf, inv);
     Flux3<T> F;
     F.a = Uf;
-    F.b = fma(Uf, uf, k.hg * Hf * Hf);
-    F.c = Vf * uf;
+    F.b = fma(Uf, uf, mul_rn(mul_rn(k.hg, Hf), Hf));
+    F.c = mul_rn(Vf, uf);
     return F;
 }
 
@@ -194,15 +255,15 @@ template <typename T>
 __device__ __forceinline__ Flux3<T> yface_flux(const CellQ<T> &D, const CellQ<T> &U, const Coef<T> &k)
 {
     const T half = T(0.5);
-    const T Hf = fma(k.hy, D.v - U.v, half * (D.h + U.h));
-    const T Uf = fma(k.hy, D.f3 - U.f3, half * (D.u + U.u));
-    const T Vf = fma(k.hy, D.g3 - U.g3, half * (D.v + U.v));
+    const T Hf = fma(k.hy, D.v - U.v, mul_rn(half, D.h + U.h));
+    const T Uf = fma(k.hy, D.f3 - U.f3, mul_rn(half, D.u + U.u));
+    const T Vf = fma(k.hy, D.g3 - U.g3, mul_rn(half, D.v + U.v));
     const T inv = rcp(Hf);
-    const T vf = Vf * inv;
+    const T vf = mul_rn(Vf, inv);
     Flux3<T> G;
     G.a = Vf;
-    G.b = Uf * vf;
-    G.c = fma(Vf, vf, k.hg * Hf * Hf);
+    G.b = mul_rn(Uf, vf);
+    G.c = fma(Vf, vf, mul_rn(mul_rn(k.hg, Hf), Hf));
     return G;
 }
 

@@ -38,8 +38,25 @@ StepGeom tiled_geom(int dtype);
 void tiled_box(int dtype, int *bw, int *bh);  // TMA box the tiled kernel loads
 
 // Reductions implemented in swe_reduce.cu.  ``scratch`` holds at least
-// reduce_scratch_doubles() doubles; results land in out_dev[0..1].
+// reduce_scratch_doubles() doubles; results land in out_dev[0..1]
+// (value, bad-cell count).
 size_t reduce_scratch_doubles();
+size_t reduce_scratch_doubles_many(int n, int B);
+
+// One grid of a batched reduction (device array of n of these).  dx, dy are
+// used by the CFL step and as the cell area of the mass.
+struct RedGrid {
+    const void *h, *u, *v;
+    long long pitch;
+    int nx, ny;
+    double dx, dy;
+};
+// Batched FP32 reductions over n grids with B blocks each; out_dev[2g] gets
+// grid g's mass or dt, out_dev[2g+1] its bad-cell count (CFL only).
+cudaError_t launch_mass_many(const RedGrid *grids_dev, int n, int B, double *scratch, double *out_dev,
+                             cudaStream_t s);
+cudaError_t launch_cfl_many(const RedGrid *grids_dev, int n, int B, double g, double cfl, double *scratch,
+                            double *out_dev, cudaStream_t s);
 cudaError_t launch_mass(int dtype, const void *H, int nx, int ny, long long pitch, double dxdy, double *scratch,
                         double *out_dev, cudaStream_t s);
 cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, int nx, int ny, long long pitch,

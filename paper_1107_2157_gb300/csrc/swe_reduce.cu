@@ -1,11 +1,11 @@
 // swe_reduce.cu -- FP64 reductions over a state plane: the mass
 // sum(h) dx dy and the CFL time step (Sec. 3).
 //
-// Both run in two launches: a fixed grid of kRedBlocks blocks writes one
-// FP64 partial per block to a scratch buffer, then one block combines the
-// partials in a fixed order.  The assignment of cells to threads and the
-// combining tree depend only on (nx, ny), so results are bitwise
-// reproducible.  The CFL per-cell terms use explicitly rounded FP64
+// A launch reduces one grid or many (blockIdx.y = instance): a fixed number
+// of blocks per grid writes one FP64 partial per block to a scratch buffer,
+// then one block per grid combines that grid's partials in a fixed order.
+// The assignment of cells to threads and the combining tree depend only on
+// the grid's size and the block count, so results are bitwise reproducible.  The CFL per-cell terms use explicitly rounded FP64
 // operations (no contraction), so the minimum is the exact minimum of
 // correctly rounded per-cell bounds.
 #include "swe_device.cuh"
@@ -16,6 +16,9 @@ constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
 size_t reduce_scratch_doubles() { return 5 * (size_t)kRedBlocks + 16; }
+
+// Scratch needed to reduce n grids with B blocks each.
+size_t reduce_scratch_doubles_many(int n, int B) { return 5 * (size_t)n * (size_t)B + 3 * (size_t)n + 16; }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -55,50 +58,64 @@ __device__ double block_reduce(double v)
     return v;
 }
 
+// Fetches the grid this block reduces: the by-value one, or grids[blockIdx.y].
+template <bool MANY>
+__device__ __forceinline__ RedGrid red_grid(const RedGrid &one, const RedGrid *__restrict__ many)
+{
+    if (MANY) return many[blockIdx.y];
+    return one;
+}
+
 // Mass partials.  Each block takes rows blockIdx.x, blockIdx.x + gridDim.x,
 // ...; with VEC the threads read 16-byte vectors (4 FP32 / 2 FP64 values,
 // the row base and stride being 16-byte aligned) and the row tail scalar.
 // Two FP64 accumulators per thread keep the adds independent.
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(kRedThreads) mass_partial_kernel(const T *__restrict__ H, int nx, int ny,
-                                                                   long long pitch, double *partial)
+template <typename T, bool VEC, bool MANY>
+__global__ void __launch_bounds__(kRedThreads) mass_partial_kernel(RedGrid one, const RedGrid *__restrict__ many,
+                                                                   double *partial)
 {
     constexpr int N = 16 / sizeof(T);
+    const RedGrid G = red_grid<MANY>(one, many);
+    const T *H = static_cast<const T *>(G.h);
     double s0 = 0.0, s1 = 0.0;
-    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
-        const T *row = H + (size_t)j * (size_t)pitch;
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+        const T *row = H + (size_t)j * (size_t)G.pitch;
         int i0 = 0;
         if (VEC) {
-            const int nv = nx / N;
-            const T *base = row;
+            const int nv = G.nx / N;
 #pragma unroll 4
             for (int v = threadIdx.x; v < nv; v += blockDim.x) {
                 if constexpr (sizeof(T) == 4) {
-                    const float4 x = __ldg(reinterpret_cast<const float4 *>(base) + v);
+                    const float4 x = __ldg(reinterpret_cast<const float4 *>(row) + v);
                     s0 += (double)x.x;
                     s1 += (double)x.y;
                     s0 += (double)x.z;
                     s1 += (double)x.w;
                 } else {
-                    const double2 x = __ldg(reinterpret_cast<const double2 *>(base) + v);
+                    const double2 x = __ldg(reinterpret_cast<const double2 *>(row) + v);
                     s0 += (double)x.x;
                     s1 += (double)x.y;
                 }
             }
             i0 = nv * N;
         }
-        for (int i = i0 + threadIdx.x; i < nx; i += blockDim.x) s0 += (double)row[i];
+        for (int i = i0 + threadIdx.x; i < G.nx; i += blockDim.x) s0 += (double)row[i];
     }
     const double s = block_reduce<false>(s0 + s1);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(1024) sum_final_kernel(const double *partial, int n, double scale, double *out)
+// One block per grid: out[2*g] = (sum of the grid's B partials) * dx * dy.
+template <bool MANY>
+__global__ void __launch_bounds__(1024) sum_final_kernel(RedGrid one, const RedGrid *__restrict__ many,
+                                                         const double *partial, int B, double *out)
 {
+    const RedGrid G = MANY ? many[blockIdx.x] : one;
+    const double *p = partial + (size_t)blockIdx.x * B;
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    for (int i = threadIdx.x; i < B; i += blockDim.x) s += p[i];
     s = block_reduce<false>(s);
-    if (threadIdx.x == 0) out[0] = s * scale;
+    if (threadIdx.x == 0) out[2 * (size_t)blockIdx.x] = s * G.dx * G.dy;
 }
 
 // ---------------------------------------------------------------------------
@@ -112,6 +129,10 @@ __global__ void __launch_bounds__(1024) sum_final_kernel(const double *partial, 
 // cell can hold the maximum.  A thread reuses its last exact value when it
 // meets the same (h, momentum) bits again, so flat regions cost one FP64
 // evaluation per thread.
+//
+// Scratch layout for n grids of B blocks (P = n*B doubles per array):
+// [0,P) ax  [P,2P) ay  [2P,3P) bad  [3P,3P+3n) thresholds (thx, thy, bad)
+// [3P+3n, 4P+3n) exact sx partials  [4P+3n, 5P+3n) exact sy partials.
 // ---------------------------------------------------------------------------
 constexpr float kCflSlack = 1.0f / 65536.0f;
 
@@ -120,16 +141,18 @@ __device__ __forceinline__ bool cell_bad(double h, double u, double v)
     return !(h > 0.0) || !isfinite(h) || !isfinite(u) || !isfinite(v);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(const T *__restrict__ H, const T *__restrict__ U,
-                                                                const T *__restrict__ V, int nx, int ny,
-                                                                long long pitch, float g32, double *scratch)
+template <typename T, bool MANY>
+__global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(RedGrid one, const RedGrid *__restrict__ many,
+                                                                float g32, double *scratch)
 {
+    const RedGrid G = red_grid<MANY>(one, many);
+    const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
+    const size_t P = (size_t)gridDim.x * gridDim.y;
     float ax = 0.0f, ay = 0.0f;
     double bad = 0.0;
-    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
-        const size_t ro = (size_t)j * (size_t)pitch;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+        const size_t ro = (size_t)j * (size_t)G.pitch;
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
             const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
             if (cell_bad((double)h, (double)u, (double)v)) {
                 bad += 1.0;
@@ -146,30 +169,33 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(const T *__restr
     ay = (float)block_reduce<false, true>((double)ay);
     bad = block_reduce<false, false>(bad);
     if (threadIdx.x == 0) {
-        scratch[blockIdx.x] = ax;
-        scratch[kRedBlocks + blockIdx.x] = ay;
-        scratch[2 * kRedBlocks + blockIdx.x] = bad;
+        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        scratch[b] = ax;
+        scratch[P + b] = ay;
+        scratch[2 * P + b] = bad;
     }
 }
 
-// Combines pass-1 partials into the pass-2 thresholds (scratch[3K..3K+2]).
-__global__ void __launch_bounds__(1024) cfl_pass1_final_kernel(double *scratch, int n)
+// One block per grid: the pass-2 thresholds of grid blockIdx.x.
+__global__ void __launch_bounds__(1024) cfl_pass1_final_kernel(double *scratch, int n, int B)
 {
+    const size_t P = (size_t)n * B;
+    const size_t o = (size_t)blockIdx.x * B;
     double ax = 0.0, ay = 0.0, bad = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        ax = fmax(ax, scratch[i]);
-        ay = fmax(ay, scratch[kRedBlocks + i]);
-        bad += scratch[2 * kRedBlocks + i];
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        ax = fmax(ax, scratch[o + i]);
+        ay = fmax(ay, scratch[P + o + i]);
+        bad += scratch[2 * P + o + i];
     }
     ax = block_reduce<false, true>(ax);
     ay = block_reduce<false, true>(ay);
     bad = block_reduce<false, false>(bad);
     if (threadIdx.x == 0) {
-        // a non-finite or tiny estimate disables the filter (every cell exact)
-        const double lo = -1.0;
-        scratch[3 * kRedBlocks + 0] = (isfinite(ax) && ax > 1e-30) ? ax * (1.0 - (double)kCflSlack) : lo;
-        scratch[3 * kRedBlocks + 1] = (isfinite(ay) && ay > 1e-30) ? ay * (1.0 - (double)kCflSlack) : lo;
-        scratch[3 * kRedBlocks + 2] = bad;
+        // a non-finite or tiny estimate disables the screen (every cell exact)
+        double *th = scratch + 3 * P + 3 * (size_t)blockIdx.x;
+        th[0] = (isfinite(ax) && ax > 1e-30) ? ax * (1.0 - (double)kCflSlack) : -1.0;
+        th[1] = (isfinite(ay) && ay > 1e-30) ? ay * (1.0 - (double)kCflSlack) : -1.0;
+        th[2] = bad;
     }
 }
 
@@ -179,20 +205,22 @@ __device__ __forceinline__ double exact_speed(double g, double h, double m)
     return __dadd_rn(__dsqrt_rn(__dmul_rn(g, h)), fabs(__ddiv_rn(m, h)));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(const T *__restrict__ H, const T *__restrict__ U,
-                                                                const T *__restrict__ V, int nx, int ny,
-                                                                long long pitch, float g32, double g,
-                                                                double *scratch)
+template <typename T, bool MANY>
+__global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, const RedGrid *__restrict__ many,
+                                                                float g32, double g, double *scratch)
 {
-    const double thx = scratch[3 * kRedBlocks + 0];
-    const double thy = scratch[3 * kRedBlocks + 1];
+    const RedGrid G = red_grid<MANY>(one, many);
+    const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
+    const size_t n = gridDim.y;
+    const size_t P = (size_t)gridDim.x * n;
+    const double *th = scratch + 3 * P + 3 * (size_t)blockIdx.y;
+    const double thx = th[0], thy = th[1];
     double sx = 0.0, sy = 0.0;
     T lhx = T(-1), lux = T(0), lhy = T(-1), lvy = T(0);  // last exactly evaluated inputs
     double lsx = 0.0, lsy = 0.0;
-    for (int j = blockIdx.x; j < ny; j += gridDim.x) {
-        const size_t ro = (size_t)j * (size_t)pitch;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+        const size_t ro = (size_t)j * (size_t)G.pitch;
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
             const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
             if (cell_bad((double)h, (double)u, (double)v)) continue;
             const float hf = (float)h;
@@ -221,72 +249,105 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(const T *__restr
     sx = block_reduce<false, true>(sx);
     sy = block_reduce<false, true>(sy);
     if (threadIdx.x == 0) {
-        scratch[3 * kRedBlocks + 8 + blockIdx.x] = sx;
-        scratch[4 * kRedBlocks + 8 + blockIdx.x] = sy;
+        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        scratch[3 * P + 3 * n + b] = sx;
+        scratch[4 * P + 3 * n + b] = sy;
     }
 }
 
-__global__ void __launch_bounds__(1024) cfl_final_kernel(const double *scratch, int n, double dx, double dy,
-                                                         double cfl, double *out)
+// One block per grid: out[2g] = dt of grid g, out[2g+1] = its bad-cell count.
+template <bool MANY>
+__global__ void __launch_bounds__(1024) cfl_final_kernel(RedGrid one, const RedGrid *__restrict__ many,
+                                                         const double *scratch, int n, int B, double cfl,
+                                                         double *out)
 {
+    const RedGrid G = MANY ? many[blockIdx.x] : one;
+    const size_t P = (size_t)n * B;
+    const size_t o = (size_t)blockIdx.x * B;
     double sx = 0.0, sy = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        sx = fmax(sx, scratch[3 * kRedBlocks + 8 + i]);
-        sy = fmax(sy, scratch[4 * kRedBlocks + 8 + i]);
+    for (int i = threadIdx.x; i < B; i += blockDim.x) {
+        sx = fmax(sx, scratch[3 * P + 3 * (size_t)n + o + i]);
+        sy = fmax(sy, scratch[4 * P + 3 * (size_t)n + o + i]);
     }
     sx = block_reduce<false, true>(sx);
     sy = block_reduce<false, true>(sy);
     if (threadIdx.x == 0) {
-        const double tx = __ddiv_rn(dx, sx), ty = __ddiv_rn(dy, sy);
-        out[0] = __dmul_rn(cfl, fmin(tx, ty));
-        out[1] = scratch[3 * kRedBlocks + 2];
+        const double tx = __ddiv_rn(G.dx, sx), ty = __ddiv_rn(G.dy, sy);
+        out[2 * (size_t)blockIdx.x] = __dmul_rn(cfl, fmin(tx, ty));
+        out[2 * (size_t)blockIdx.x + 1] = scratch[3 * P + 3 * (size_t)blockIdx.x + 2];
     }
 }
 
 static int red_blocks(int ny) { return ny < kRedBlocks ? ny : kRedBlocks; }
 
+static bool plane_vec_ok(const void *H, long long pitch, size_t es)
+{
+    return ((uintptr_t)H % 16 == 0) && (((size_t)pitch * es) % 16 == 0);
+}
+
+template <typename T, bool MANY>
+static void mass_launch(const RedGrid &one, const RedGrid *many, int n, int B, bool vec, double *scratch,
+                        double *out, cudaStream_t s)
+{
+    const dim3 grid(B, n);
+    if (vec)
+        mass_partial_kernel<T, true, MANY><<<grid, kRedThreads, 0, s>>>(one, many, scratch);
+    else
+        mass_partial_kernel<T, false, MANY><<<grid, kRedThreads, 0, s>>>(one, many, scratch);
+    sum_final_kernel<MANY><<<n, 1024, 0, s>>>(one, many, scratch, B, out);
+}
+
 cudaError_t launch_mass(int dtype, const void *H, int nx, int ny, long long pitch, double dxdy, double *scratch,
                         double *out_dev, cudaStream_t s)
 {
-    const int nb = red_blocks(ny);
+    RedGrid one{H, nullptr, nullptr, pitch, nx, ny, dxdy, 1.0};
     const size_t es = dtype == SWE_F64 ? 8 : 4;
-    const bool vec = ((uintptr_t)H % 16 == 0) && (((size_t)pitch * es) % 16 == 0);
-    if (dtype == SWE_F64) {
-        const double *h = static_cast<const double *>(H);
-        if (vec)
-            mass_partial_kernel<double, true><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
-        else
-            mass_partial_kernel<double, false><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
-    } else {
-        const float *h = static_cast<const float *>(H);
-        if (vec)
-            mass_partial_kernel<float, true><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
-        else
-            mass_partial_kernel<float, false><<<nb, kRedThreads, 0, s>>>(h, nx, ny, pitch, scratch);
-    }
-    sum_final_kernel<<<1, 1024, 0, s>>>(scratch, nb, dxdy, out_dev);
+    const int B = red_blocks(ny);
+    if (dtype == SWE_F64)
+        mass_launch<double, false>(one, nullptr, 1, B, plane_vec_ok(H, pitch, es), scratch, out_dev, s);
+    else
+        mass_launch<float, false>(one, nullptr, 1, B, plane_vec_ok(H, pitch, es), scratch, out_dev, s);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mass_many(const RedGrid *grids_dev, int n, int B, double *scratch, double *out_dev,
+                             cudaStream_t s)
+{
+    // batched planes are FP32 with 128-byte aligned rows
+    RedGrid none{};
+    mass_launch<float, true>(none, grids_dev, n, B, true, scratch, out_dev, s);
+    return cudaGetLastError();
+}
+
+template <typename T, bool MANY>
+static void cfl_launch(const RedGrid &one, const RedGrid *many, int n, int B, double g, double cfl, double *scratch,
+                       double *out, cudaStream_t s)
+{
+    const dim3 grid(B, n);
+    const float g32 = (float)g;
+    cfl_pass1_kernel<T, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, scratch);
+    cfl_pass1_final_kernel<<<n, 1024, 0, s>>>(scratch, n, B);
+    cfl_pass2_kernel<T, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, g, scratch);
+    cfl_final_kernel<MANY><<<n, 1024, 0, s>>>(one, many, scratch, n, B, cfl, out);
 }
 
 cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, int nx, int ny, long long pitch,
                        double dx, double dy, double g, double cfl, double *scratch, double *out_dev, cudaStream_t s)
 {
-    const int nb = red_blocks(ny);
-    const float g32 = (float)g;
-    if (dtype == SWE_F64) {
-        const double *h = static_cast<const double *>(H), *u = static_cast<const double *>(U),
-                     *v = static_cast<const double *>(V);
-        cfl_pass1_kernel<double><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, scratch);
-        cfl_pass1_final_kernel<<<1, 1024, 0, s>>>(scratch, nb);
-        cfl_pass2_kernel<double><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, g, scratch);
-    } else {
-        const float *h = static_cast<const float *>(H), *u = static_cast<const float *>(U),
-                    *v = static_cast<const float *>(V);
-        cfl_pass1_kernel<float><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, scratch);
-        cfl_pass1_final_kernel<<<1, 1024, 0, s>>>(scratch, nb);
-        cfl_pass2_kernel<float><<<nb, kRedThreads, 0, s>>>(h, u, v, nx, ny, pitch, g32, g, scratch);
-    }
-    cfl_final_kernel<<<1, 1024, 0, s>>>(scratch, nb, dx, dy, cfl, out_dev);
+    RedGrid one{H, U, V, pitch, nx, ny, dx, dy};
+    const int B = red_blocks(ny);
+    if (dtype == SWE_F64)
+        cfl_launch<double, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+    else
+        cfl_launch<float, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_many(const RedGrid *grids_dev, int n, int B, double g, double cfl, double *scratch,
+                            double *out_dev, cudaStream_t s)
+{
+    RedGrid none{};
+    cfl_launch<float, true>(none, grids_dev, n, B, g, cfl, scratch, out_dev, s);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,10 @@ LIB_PATH = os.path.join(HERE, "libswe.so")
 SWE_OK, SWE_EINVAL, SWE_ENOMEM, SWE_ECUDA, SWE_ETIMEOUT, SWE_ECHECK, SWE_EUNSUPPORTED = range(7)
 SWE_F32, SWE_F64 = 0, 1
 SWE_KERNEL_AUTO, SWE_KERNEL_NAIVE, SWE_KERNEL_TILED, SWE_KERNEL_TEMPORAL = range(4)
+SWE_FLAG_NONPOSITIVE, SWE_FLAG_MASS, SWE_FLAG_TIMEOUT, SWE_FLAG_FALLBACK = 1, 2, 4, 8
+(SWE_BQ_VARIANT, SWE_BQ_CTAS_PER_SM, SWE_BQ_BLOCKS, SWE_BQ_TILES, SWE_BQ_TILE_X, SWE_BQ_TILE_Y,
+ SWE_BQ_STAGES, SWE_BQ_DEPTH, SWE_BQ_GRAPH, SWE_BQ_LAUNCHES, SWE_BQ_TUNED, SWE_BQ_CELLS,
+ SWE_BQ_VARIANT_COUNT) = range(13)
 (SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
  SWE_Q_STATE_PTR) = range(7)
 
@@ -56,6 +60,19 @@ _SIGS = {
     "swe_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_strerror": (ctypes.c_char_p, [_i]),
     "swe_mass_noalloc": (_i, [_i, _vp, _i, _i, _ll, _d, _d, _vp, _vp]),
+    "swe_batch_create": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(_vp)]),
+    "swe_batch_destroy": (None, [_vp]),
+    "swe_batch_set_state": (_i, [_vp, _i, _vp, _vp, _vp, _ll, _i, _vp]),
+    "swe_batch_get_state": (_i, [_vp, _i, _vp, _vp, _vp, _ll, _i, _vp]),
+    "swe_batch_set_dt": (_i, [_vp, _vp, _vp]),
+    "swe_batch_step": (_i, [_vp, _i, _vp]),
+    "swe_batch_status": (_i, [_vp, _vp, _vp]),
+    "swe_batch_mass": (_i, [_vp, _vp, _vp]),
+    "swe_batch_cfl_dt": (_i, [_vp, _d, _vp, _vp]),
+    "swe_batch_tune": (_i, [_vp, ctypes.c_char_p, _vp]),
+    "swe_batch_configure": (_i, [_vp, _i, _i]),
+    "swe_batch_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
+    "swe_selftest_wait": (_i, [_i, _d, _vp]),
 }
 
 
@@ -254,3 +271,102 @@ class Grid:
 
     def query(self, key):
         return swe_query(self.ctx, key)
+
+
+# --- batched ensembles ----------------------------------------------------------------------
+
+def _dptr(a):
+    return a.ctypes.data_as(_vp)
+
+
+class Batch:
+    """Many FP32 grids stepped together (owns a swe_batch)."""
+
+    def __init__(self, sizes, dx, dy, dt, g):
+        n = len(sizes)
+        self.n = n
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        self._nx = np.array([s[0] for s in self.sizes], np.int32)
+        self._ny = np.array([s[1] for s in self.sizes], np.int32)
+        self._dx = np.ascontiguousarray(np.broadcast_to(np.asarray(dx, np.float64), (n,)))
+        self._dy = np.ascontiguousarray(np.broadcast_to(np.asarray(dy, np.float64), (n,)))
+        dtv = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (n,)))
+        h = _vp()
+        check(lib().swe_batch_create(n, _dptr(self._nx), _dptr(self._ny), _dptr(self._dx), _dptr(self._dy),
+                                     _dptr(dtv), g, ctypes.byref(h)), "swe_batch_create")
+        self.b = h.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().swe_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, i, h, hu, hv, stream=None):
+        bufs = [_buf(a, np.float32) for a in (h, hu, hv)]
+        check(lib().swe_batch_set_state(self.b, i, bufs[0][0], bufs[1][0], bufs[2][0], bufs[0][1], bufs[0][2],
+                                        stream if stream is not None else current_stream()),
+              "swe_batch_set_state")
+
+    def get_state(self, i, out=None, stream=None, sync=True):
+        nx, ny = self.sizes[i]
+        if out is None:
+            out = [np.empty((ny, nx), np.float32) for _ in range(3)]
+        bufs = [_buf(a, np.float32) for a in out]
+        check(lib().swe_batch_get_state(self.b, i, bufs[0][0], bufs[1][0], bufs[2][0], bufs[0][1], bufs[0][2],
+                                        stream if stream is not None else current_stream()),
+              "swe_batch_get_state")
+        if sync:
+            import torch
+            torch.cuda.synchronize()
+        return out
+
+    def set_dt(self, dt, stream=None):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (self.n,)))
+        check(lib().swe_batch_set_dt(self.b, _dptr(d), stream if stream is not None else current_stream()),
+              "swe_batch_set_dt")
+
+    def step(self, n, stream=None):
+        check(lib().swe_batch_step(self.b, int(n), stream if stream is not None else current_stream()),
+              "swe_batch_step")
+
+    def status(self, stream=None):
+        f = np.zeros(self.n, np.int32)
+        rc = lib().swe_batch_status(self.b, _dptr(f), stream if stream is not None else current_stream())
+        return rc, f
+
+    def mass(self, stream=None):
+        m = np.zeros(self.n, np.float64)
+        check(lib().swe_batch_mass(self.b, _dptr(m), stream if stream is not None else current_stream()),
+              "swe_batch_mass")
+        return m
+
+    def cfl_dt(self, cfl, stream=None):
+        d = np.zeros(self.n, np.float64)
+        check(lib().swe_batch_cfl_dt(self.b, cfl, _dptr(d), stream if stream is not None else current_stream()),
+              "swe_batch_cfl_dt")
+        return d
+
+    def tune(self, cache_path=None, stream=None):
+        p = cache_path.encode() if cache_path else None
+        check(lib().swe_batch_tune(self.b, p, stream if stream is not None else current_stream()),
+              "swe_batch_tune")
+
+    def configure(self, variant, ctas_per_sm):
+        check(lib().swe_batch_configure(self.b, int(variant), int(ctas_per_sm)), "swe_batch_configure")
+
+    def query(self, key):
+        v = _ll()
+        check(lib().swe_batch_query(self.b, int(key), ctypes.byref(v)), "swe_batch_query")
+        return v.value
