@@ -255,6 +255,10 @@ swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream);
  */
 swe_status swe_selftest_wait(int which, double limit_ms, void *stream);
 
+/* Device address of instance i's h plane in the current buffer, and the
+ * plane stride and row pitch in floats (hu, hv follow at +1, +2 planes). */
+swe_status swe_batch_state_ptr(swe_batch *b, int i, float **h, long long *plane_stride, long long *pitch);
+
 /* Selects a kernel variant and CTAs per SM explicitly (tests, tuning). */
 swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm);
 
@@ -268,6 +272,66 @@ typedef enum {
     SWE_BQ_VARIANT_COUNT = 12
 } swe_batch_query_key;
 swe_status swe_batch_query(swe_batch *b, int key, long long *value);
+
+/* ==========================================================================
+ * Learned coarse-grid corrector (no counterpart in the paper).  A network
+ * of zero-padded 3x3 convolutions, 3 -> 32 -> 32 -> 3 channels with GELU
+ * (0.5 z (1 + erf(z / sqrt 2))), BF16 weights and activations with FP32
+ * accumulation on the tcgen05 tensor cores, predicts the residual that
+ * carries a coarse Lax-Wendroff step (Sec. 3) toward the 4x4 block
+ * average of the fine solution.  Images are H x W coarse grids.
+ *
+ * Parameters (FP32 master copy, swe_net_param_count() floats, in order):
+ * W1[3][3][3][32], b1[32], W2[3][3][32][32], b2[32], W3[3][3][32][3], b3[3],
+ * with W[ky][kx][c_in][c_out] applied as y[o](i,j) = b[o] +
+ * sum W[ky][kx][c][o] x[c](i+ky-1, j+kx-1).
+ * Normalisation (swe_net_set_norm, 5 floats): h0, sh, su (network input
+ * ((h - h0)/sh, hu/su, hv/su)) and oh, ou (output scale of the h and
+ * momentum residuals).  State arguments are FP32 device pointers to image
+ * 0's h plane; image i's field f row y starts at
+ * state + i*img_stride + f*plane_stride + y*pitch (all in floats).
+ * ========================================================================== */
+typedef struct swe_net swe_net;
+
+size_t swe_net_param_count(void);
+/* Allocates activations for up to max_images images of H x W (<= 8192). */
+swe_status swe_net_create(int max_images, int H, int W, swe_net **out);
+void swe_net_destroy(swe_net *net);
+/* Host FP32 parameters in / out; setting them resets the optimiser state. */
+swe_status swe_net_set_params(swe_net *net, const float *params);
+swe_status swe_net_get_params(swe_net *net, float *params);
+swe_status swe_net_set_norm(swe_net *net, const float *norm5);
+/* Builds the network input of n images from a state (stream-ordered). */
+swe_status swe_net_prep_input(swe_net *net, int n, const float *state, long long img_stride,
+                              long long plane_stride, long long pitch, void *stream);
+/* Inference on the prepared input: residual in physical units, FP32
+ * [n][3][H][W] into resid (device; NULL = the net's own buffer). */
+swe_status swe_net_infer(swe_net *net, int n, float *resid, void *stream);
+/* state += residual (the net's own buffer, from swe_net_infer(.., NULL, ..));
+ * with project_mass the h residual's mean is removed per image first, so
+ * the corrected step keeps the Lax-Wendroff step's mass. */
+swe_status swe_net_apply(swe_net *net, int n, float *state, long long img_stride, long long plane_stride,
+                         long long pitch, int project_mass, void *stream);
+/* Training target (normalised): (next - lw) / (oh, ou, ou), FP32 [n][3][H][W];
+ * next is FP32 [n][3][H][W] contiguous, lw a state as above. */
+swe_status swe_net_make_target(swe_net *net, int n, const float *next, const float *lw, long long img_stride,
+                               long long plane_stride, long long pitch, float *target, void *stream);
+/* One training step on the prepared input: forward, mean squared error
+ * against target, backward (tcgen05 input gradients, CUDA-core weight
+ * gradients), and with update = 1 an AdamW step (lr, weight decay wd,
+ * global-norm clip if clip > 0).  Synchronous.  Optional outputs: the loss,
+ * the gradients (host, param_count floats), the raw network output r
+ * (device FP32 [n][3][H][W]). */
+swe_status swe_net_train_step(swe_net *net, int n, const float *target, float lr, float wd, float clip, int update,
+                              double *loss_out, float *grads_out, float *resid_out, void *stream);
+/* Synchronises and returns the device error word of the net's kernels. */
+swe_status swe_net_check(swe_net *net, void *stream);
+/* 4x4 block average of n images (3 planes each) of 4Hc x 4Wc fine cells:
+ * strides in floats as above; the fine pointer, pitch and strides must be
+ * 16-byte multiples. */
+swe_status swe_downsample4(const float *fine, long long f_img, long long f_plane, long long f_pitch, float *coarse,
+                           long long c_img, long long c_plane, long long c_pitch, int Wc, int Hc, int n,
+                           void *stream);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,26 @@ bool encode_plane_map(CUtensorMap *map, int dtype, const void *base, int nx, int
     return r == CUDA_SUCCESS;
 }
 
+// 5D map over a row-chunked bf16 activation tensor [N][H][CH][W][8]:
+// dims {8, W, CH, H, N}; box {8, 130, CH, box_rows, 1}.
+bool encode_act_map(CUtensorMap *map, const void *base, int W, int H, int CH, int N, int box_rows)
+{
+    if (!g_encode) {
+        CUtensorMap dummy;
+        float one = 0.0f;
+        (void)encode_plane_map(&dummy, SWE_F32, &one, 1, 1, 32, 4, 1);  // resolves the entry point
+    }
+    if (!g_encode) return false;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)CH, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)CH * W * 16, (cuuint64_t)H * CH * W * 16};
+    const cuuint32_t box[5] = {8, 130, (cuuint32_t)CH, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 }  // namespace swe
 
 using namespace swe;

@@ -745,6 +745,15 @@ swe_status swe_selftest_wait(int which, double limit_ms, void *stream)
     return (swe_status)word;
 }
 
+swe_status swe_batch_state_ptr(swe_batch *b, int i, float **h, long long *plane_stride, long long *pitch)
+{
+    if (!b || !h || !plane_stride || !pitch || i < 0 || i >= b->n) return SWE_EINVAL;
+    *h = b->h_inst[i].buf[b->cur];
+    *plane_stride = b->h_inst[i].plane;
+    *pitch = b->h_inst[i].pitch;
+    return SWE_OK;
+}
+
 swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm)
 {
     if (!b || variant < 0 || variant >= (int)variants().size() || ctas_per_sm < 1) return SWE_EINVAL;

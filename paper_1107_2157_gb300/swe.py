@@ -73,6 +73,21 @@ _SIGS = {
     "swe_batch_configure": (_i, [_vp, _i, _i]),
     "swe_batch_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_selftest_wait": (_i, [_i, _d, _vp]),
+    "swe_batch_state_ptr": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "swe_net_param_count": (ctypes.c_size_t, []),
+    "swe_net_create": (_i, [_i, _i, _i, ctypes.POINTER(_vp)]),
+    "swe_net_destroy": (None, [_vp]),
+    "swe_net_set_params": (_i, [_vp, _vp]),
+    "swe_net_get_params": (_i, [_vp, _vp]),
+    "swe_net_set_norm": (_i, [_vp, _vp]),
+    "swe_net_prep_input": (_i, [_vp, _i, _vp, _ll, _ll, _ll, _vp]),
+    "swe_net_infer": (_i, [_vp, _i, _vp, _vp]),
+    "swe_net_apply": (_i, [_vp, _i, _vp, _ll, _ll, _ll, _i, _vp]),
+    "swe_net_make_target": (_i, [_vp, _i, _vp, _vp, _ll, _ll, _ll, _vp, _vp]),
+    "swe_net_train_step": (_i, [_vp, _i, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i,
+                                ctypes.POINTER(_d), _vp, _vp, _vp]),
+    "swe_net_check": (_i, [_vp, _vp]),
+    "swe_downsample4": (_i, [_vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
 
 
@@ -370,3 +385,105 @@ class Batch:
         v = _ll()
         check(lib().swe_batch_query(self.b, int(key), ctypes.byref(v)), "swe_batch_query")
         return v.value
+
+    def state_ptr(self, i):
+        """(device address of instance i's h plane, plane stride, pitch)."""
+        p, ps, pi = _vp(), _ll(), _ll()
+        check(lib().swe_batch_state_ptr(self.b, int(i), ctypes.byref(p), ctypes.byref(ps), ctypes.byref(pi)),
+              "swe_batch_state_ptr")
+        return p.value, ps.value, pi.value
+
+
+# --- learned corrector -------------------------------------------------------------------------
+
+PARAM_SHAPES = [("W1", (3, 3, 3, 32)), ("b1", (32,)), ("W2", (3, 3, 32, 32)), ("b2", (32,)),
+                ("W3", (3, 3, 32, 3)), ("b3", (3,))]
+
+
+def flatten_params(params) -> np.ndarray:
+    """dict of arrays (W[ky][kx][c_in][c_out], b[c_out]) -> flat float32."""
+    return np.concatenate([np.asarray(params[k], np.float32).reshape(-1) for k, _ in PARAM_SHAPES])
+
+
+def unflatten_params(flat):
+    out, o = {}, 0
+    for k, shp in PARAM_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n], np.float64).reshape(shp)
+        o += n
+    return out
+
+
+class Net:
+    """The corrector network on the current device (owns a swe_net)."""
+
+    def __init__(self, max_images, H, W):
+        h = _vp()
+        check(lib().swe_net_create(int(max_images), int(H), int(W), ctypes.byref(h)), "swe_net_create")
+        self.t = h.value
+        self.H, self.W, self.max_images = H, W, max_images
+        self.nparams = int(lib().swe_net_param_count())
+
+    def close(self):
+        if getattr(self, "t", None):
+            lib().swe_net_destroy(self.t)
+            self.t = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, np.float32)
+        assert a.size == self.nparams
+        check(lib().swe_net_set_params(self.t, a.ctypes.data), "swe_net_set_params")
+
+    def get_params(self):
+        a = np.zeros(self.nparams, np.float32)
+        check(lib().swe_net_get_params(self.t, a.ctypes.data), "swe_net_get_params")
+        return a
+
+    def set_norm(self, h0, sh, su, oh, ou):
+        a = np.array([h0, sh, su, oh, ou], np.float32)
+        check(lib().swe_net_set_norm(self.t, a.ctypes.data), "swe_net_set_norm")
+
+    def prep_input(self, n, state_ptr, img_stride, plane_stride, pitch, stream=None):
+        check(lib().swe_net_prep_input(self.t, n, state_ptr, img_stride, plane_stride, pitch,
+                                       stream if stream is not None else current_stream()), "swe_net_prep_input")
+
+    def infer(self, n, resid_ptr=None, stream=None):
+        check(lib().swe_net_infer(self.t, n, resid_ptr, stream if stream is not None else current_stream()),
+              "swe_net_infer")
+
+    def apply(self, n, state_ptr, img_stride, plane_stride, pitch, project_mass=True, stream=None):
+        check(lib().swe_net_apply(self.t, n, state_ptr, img_stride, plane_stride, pitch, int(project_mass),
+                                  stream if stream is not None else current_stream()), "swe_net_apply")
+
+    def make_target(self, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, target_ptr, stream=None):
+        check(lib().swe_net_make_target(self.t, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, target_ptr,
+                                        stream if stream is not None else current_stream()), "swe_net_make_target")
+
+    def train_step(self, n, target_ptr, lr=1e-3, wd=0.0, clip=0.0, update=True, want_grads=False,
+                   resid_ptr=None, stream=None):
+        loss = _d()
+        g = np.zeros(self.nparams, np.float32) if want_grads else None
+        check(lib().swe_net_train_step(self.t, n, target_ptr, lr, wd, clip, int(update), ctypes.byref(loss),
+                                       g.ctypes.data if g is not None else None, resid_ptr,
+                                       stream if stream is not None else current_stream()), "swe_net_train_step")
+        return loss.value, g
+
+    def check(self, stream=None):
+        return int(lib().swe_net_check(self.t, stream if stream is not None else current_stream()))
+
+
+def swe_downsample4(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n, stream=None):
+    check(lib().swe_downsample4(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n,
+                                stream if stream is not None else current_stream()), "swe_downsample4")
