@@ -259,6 +259,10 @@ swe_status swe_selftest_wait(int which, double limit_ms, void *stream);
  * plane stride and row pitch in floats (hu, hv follow at +1, +2 planes). */
 swe_status swe_batch_state_ptr(swe_batch *b, int i, float **h, long long *plane_stride, long long *pitch);
 
+/* Copies every instance's current state, in order, to a contiguous device
+ * buffer: instance i's h, hu, hv planes of ny[i] x nx[i] floats each. */
+swe_status swe_batch_copy_states(swe_batch *b, float *dst, void *stream);
+
 /* Selects a kernel variant and CTAs per SM explicitly (tests, tuning). */
 swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm);
 
@@ -301,8 +305,13 @@ void swe_net_destroy(swe_net *net);
 swe_status swe_net_set_params(swe_net *net, const float *params);
 swe_status swe_net_get_params(swe_net *net, float *params);
 swe_status swe_net_set_norm(swe_net *net, const float *norm5);
-/* Builds the network input of n images from a state (stream-ordered). */
-swe_status swe_net_prep_input(swe_net *net, int n, const float *state, long long img_stride,
+/* Builds the network input of n images from a state (stream-ordered):
+ * ((h - h0)/sh, hu/su, hv/su), or, with a second state ``base`` (same
+ * strides, may be NULL), the FP32 difference (state - base) scaled by
+ * (1/sh, 1/su, 1/su).  The corrector uses the latter with state = the coarse
+ * Lax-Wendroff result and base = the state it started from, so the network
+ * sees the step's increment at FP32 resolution before the BF16 rounding. */
+swe_status swe_net_prep_input(swe_net *net, int n, const float *state, const float *base, long long img_stride,
                               long long plane_stride, long long pitch, void *stream);
 /* Inference on the prepared input: residual in physical units, FP32
  * [n][3][H][W] into resid (device; NULL = the net's own buffer). */
@@ -312,10 +321,11 @@ swe_status swe_net_infer(swe_net *net, int n, float *resid, void *stream);
  * the corrected step keeps the Lax-Wendroff step's mass. */
 swe_status swe_net_apply(swe_net *net, int n, float *state, long long img_stride, long long plane_stride,
                          long long pitch, int project_mass, void *stream);
-/* Training target (normalised): (next - lw) / (oh, ou, ou), FP32 [n][3][H][W];
- * next is FP32 [n][3][H][W] contiguous, lw a state as above. */
+/* Training target (normalised): (next - lw) / (oh, ou, ou), clipped to
+ * [-clip, clip] if clip > 0, FP32 [n][3][H][W]; next is FP32 [n][3][H][W]
+ * contiguous, lw a state as above. */
 swe_status swe_net_make_target(swe_net *net, int n, const float *next, const float *lw, long long img_stride,
-                               long long plane_stride, long long pitch, float *target, void *stream);
+                               long long plane_stride, long long pitch, float clip, float *target, void *stream);
 /* One training step on the prepared input: forward, mean squared error
  * against target, backward (tcgen05 input gradients, CUDA-core weight
  * gradients), and with update = 1 an AdamW step (lr, weight decay wd,
@@ -326,12 +336,13 @@ swe_status swe_net_train_step(swe_net *net, int n, const float *target, float lr
                               double *loss_out, float *grads_out, float *resid_out, void *stream);
 /* Synchronises and returns the device error word of the net's kernels. */
 swe_status swe_net_check(swe_net *net, void *stream);
-/* 4x4 block average of n images (3 planes each) of 4Hc x 4Wc fine cells:
- * strides in floats as above; the fine pointer, pitch and strides must be
- * 16-byte multiples. */
-swe_status swe_downsample4(const float *fine, long long f_img, long long f_plane, long long f_pitch, float *coarse,
-                           long long c_img, long long c_plane, long long c_pitch, int Wc, int Hc, int n,
-                           void *stream);
+/* factor x factor block average (factor 1..4) of n images (3 planes each)
+ * of (factor Hc) x (factor Wc) fine cells into Hc x Wc coarse cells; strides
+ * in floats as above.  The restriction that turns a fine solution into the
+ * coarse target.  Stream-ordered. */
+swe_status swe_downsample(int factor, const float *fine, long long f_img, long long f_plane, long long f_pitch,
+                          float *coarse, long long c_img, long long c_plane, long long c_pitch, int Wc, int Hc, int n,
+                          void *stream);
 
 #ifdef __cplusplus
 }

@@ -116,8 +116,13 @@ def init_params(seed: int, cin=3, hidden=32, cout=3, out_scale=0.1):
                 W3=w(hidden, cout, out_scale), b3=np.zeros(cout))
 
 
+def block_average(u: np.ndarray, f: int) -> np.ndarray:
+    """f x f block average of the last two axes (sizes divisible by f)."""
+    H, W = u.shape[-2], u.shape[-1]
+    v = u.reshape(u.shape[:-2] + (H // f, f, W // f, f))
+    return v.sum(axis=(-3, -1)) / float(f * f)
+
+
 def downsample4(u: np.ndarray) -> np.ndarray:
     """4x4 block average of the last two axes (sizes divisible by 4)."""
-    H, W = u.shape[-2], u.shape[-1]
-    v = u.reshape(u.shape[:-2] + (H // 4, 4, W // 4, 4))
-    return v.sum(axis=(-3, -1)) / 16.0
+    return block_average(u, 4)

@@ -754,6 +754,23 @@ swe_status swe_batch_state_ptr(swe_batch *b, int i, float **h, long long *plane_
     return SWE_OK;
 }
 
+swe_status swe_batch_copy_states(swe_batch *b, float *dst, void *stream)
+{
+    if (!b || !dst) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t at = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const BatchInst &I = b->h_inst[i];
+        for (int k = 0; k < 3; ++k) {
+            B_TRY(cudaMemcpy2DAsync(dst + at, (size_t)I.nx * sizeof(float), I.buf[b->cur] + k * I.plane,
+                                    (size_t)I.pitch * sizeof(float), (size_t)I.nx * sizeof(float), I.ny,
+                                    cudaMemcpyDeviceToDevice, s));
+            at += (size_t)I.nx * I.ny;
+        }
+    }
+    return SWE_OK;
+}
+
 swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm)
 {
     if (!b || variant < 0 || variant >= (int)variants().size() || ctas_per_sm < 1) return SWE_EINVAL;

@@ -241,10 +241,12 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
 // ---------------------------------------------------------------------------
 
 // FP32 state planes (3 per image, rows of ``pitch``) -> row-chunked bf16 input
-// with 16 channels: (h - h0)/sh, hu/su, hv/su, then zeros.
-__global__ void prep_input_kernel(const float *__restrict__ state, long long img_stride, long long plane_stride,
-                                  long long pitch, int W, int H, int n, float h0, float inv_sh, float inv_su,
-                                  bf16 *__restrict__ x0)
+// with 16 channels: (h - h0)/sh, hu/su, hv/su, then zeros.  With a second
+// state ``base`` the input is the difference (state - base) instead:
+// (dh/sh, dhu/su, dhv/su), formed in FP32 before the rounding to bf16.
+__global__ void prep_input_kernel(const float *__restrict__ state, const float *__restrict__ base,
+                                  long long img_stride, long long plane_stride, long long pitch, int W, int H, int n,
+                                  float h0, float inv_sh, float inv_su, bf16 *__restrict__ x0)
 {
     const long long total = (long long)n * H * W;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
@@ -252,42 +254,48 @@ __global__ void prep_input_kernel(const float *__restrict__ state, long long img
         const int x = (int)(p % W);
         const int y = (int)((p / W) % H);
         const int i = (int)(p / ((long long)W * H));
-        const float *s = state + i * img_stride + (long long)y * pitch + x;
+        const long long o = i * img_stride + (long long)y * pitch + x;
+        const float *s = state + o;
+        float f0 = s[0] - h0, f1 = s[plane_stride], f2 = s[2 * plane_stride];
+        if (base) {
+            const float *b = base + o;
+            f0 = s[0] - b[0];
+            f1 -= b[plane_stride];
+            f2 -= b[2 * plane_stride];
+        }
         __align__(16) bf16 c8[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) c8[k] = __float2bfloat16_rn(0.0f);
-        c8[0] = __float2bfloat16_rn((s[0] - h0) * inv_sh);
-        c8[1] = __float2bfloat16_rn(s[plane_stride] * inv_su);
-        c8[2] = __float2bfloat16_rn(s[2 * plane_stride] * inv_su);
+        c8[0] = __float2bfloat16_rn(f0 * inv_sh);
+        c8[1] = __float2bfloat16_rn(f1 * inv_su);
+        c8[2] = __float2bfloat16_rn(f2 * inv_su);
         *reinterpret_cast<uint4 *>(x0 + rc_index(i, y, 0, x, H, W, 2)) = *reinterpret_cast<const uint4 *>(c8);
         *reinterpret_cast<uint4 *>(x0 + rc_index(i, y, 1, x, H, W, 2)) = *reinterpret_cast<const uint4 *>(c8 + 8);
     }
 }
 
-// 4x4 block average of FP32 planes: fine [n][3] planes (rows of fpitch) ->
-// coarse planes (rows of cpitch).  The 16 values are summed row by row.
-__global__ void downsample4_kernel(const float *__restrict__ fine, long long f_img, long long f_plane,
-                                   long long fpitch, float *__restrict__ coarse, long long c_img, long long c_plane,
-                                   long long cpitch, int Wc, int Hc, int n)
+// F x F block average of FP32 planes: fine [n][3] planes (rows of fpitch) ->
+// coarse planes (rows of cpitch).  The F*F values are summed row by row.
+template <int F>
+__global__ void downsample_kernel(const float *__restrict__ fine, long long f_img, long long f_plane, long long fpitch,
+                                  float *__restrict__ coarse, long long c_img, long long c_plane, long long cpitch,
+                                  int Wc, int Hc, int n)
 {
     const long long total = (long long)n * 3 * Hc * Wc;
+    const float inv = 1.0f / (float)(F * F);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
          p += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(p % Wc);
         const int Y = (int)((p / Wc) % Hc);
         const int f = (int)((p / ((long long)Wc * Hc)) % 3);
         const int i = (int)(p / ((long long)Wc * Hc * 3));
-        const float *src = fine + i * f_img + f * f_plane + (long long)(4 * Y) * fpitch + 4 * X;
+        const float *src = fine + i * f_img + f * f_plane + (long long)(F * Y) * fpitch + F * X;
         float s = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const float4 q = *reinterpret_cast<const float4 *>(src + a * fpitch);
-            s += q.x;
-            s += q.y;
-            s += q.z;
-            s += q.w;
-        }
-        coarse[i * c_img + f * c_plane + (long long)Y * cpitch + X] = s * 0.0625f;
+        for (int a = 0; a < F; ++a)
+#pragma unroll
+            for (int b = 0; b < F; ++b) s += src[a * fpitch + b];
+        coarse[i * c_img + f * c_plane + (long long)Y * cpitch + X] = s * inv;
     }
 }
 
@@ -486,10 +494,11 @@ __global__ void __launch_bounds__(1024) apply_correction_kernel(float *__restric
     }
 }
 
-// target[n][c][y][x] = (next[n][c][y][x] - lw_c(y, x)) * inv_scale[c]
+// target[n][c][y][x] = (next[n][c][y][x] - lw_c(y, x)) * inv_scale[c], clipped
+// to [-clip, clip] when clip > 0.
 __global__ void make_target_kernel(const float *__restrict__ next, const float *__restrict__ lw, long long img_stride,
                                    long long plane_stride, long long pitch, int W, int H, int n, float is_h,
-                                   float is_u, float *__restrict__ target)
+                                   float is_u, float clip, float *__restrict__ target)
 {
     const long long plane = (long long)H * W;
     const long long total = (long long)n * 3 * plane;
@@ -500,7 +509,9 @@ __global__ void make_target_kernel(const float *__restrict__ next, const float *
         const int c = (int)((e / plane) % 3);
         const int i = (int)(e / (3 * plane));
         const float l = lw[i * img_stride + c * plane_stride + (long long)y * pitch + x];
-        target[e] = (next[e] - l) * (c == 0 ? is_h : is_u);
+        float t = (next[e] - l) * (c == 0 ? is_h : is_u);
+        if (clip > 0.0f) t = fminf(fmaxf(t, -clip), clip);
+        target[e] = t;
     }
 }
 
@@ -698,12 +709,12 @@ swe_status swe_net_set_norm(swe_net *t, const float *norm5)
     return SWE_OK;
 }
 
-swe_status swe_net_prep_input(swe_net *t, int n, const float *state, long long img_stride, long long plane_stride,
-                              long long pitch, void *stream)
+swe_status swe_net_prep_input(swe_net *t, int n, const float *state, const float *base, long long img_stride,
+                              long long plane_stride, long long pitch, void *stream)
 {
     if (!t || !state || n < 1 || n > t->max_n || pitch < t->W) return SWE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    prep_input_kernel<<<1184, 256, 0, s>>>(state, img_stride, plane_stride, pitch, t->W, t->H, n, t->norm[0],
+    prep_input_kernel<<<1184, 256, 0, s>>>(state, base, img_stride, plane_stride, pitch, t->W, t->H, n, t->norm[0],
                                            1.0f / t->norm[1], 1.0f / t->norm[2], t->x0);
     return nst(cudaGetLastError());
 }
@@ -750,12 +761,12 @@ swe_status swe_net_apply(swe_net *t, int n, float *state, long long img_stride, 
 }
 
 swe_status swe_net_make_target(swe_net *t, int n, const float *next, const float *lw, long long img_stride,
-                               long long plane_stride, long long pitch, float *target, void *stream)
+                               long long plane_stride, long long pitch, float clip, float *target, void *stream)
 {
-    if (!t || !next || !lw || !target || n < 1) return SWE_EINVAL;
+    if (!t || !next || !lw || !target || n < 1 || !(clip >= 0.0f)) return SWE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     make_target_kernel<<<1184, 256, 0, s>>>(next, lw, img_stride, plane_stride, pitch, t->W, t->H, n,
-                                            1.0f / t->norm[3], 1.0f / t->norm[4], target);
+                                            1.0f / t->norm[3], 1.0f / t->norm[4], clip, target);
     return nst(cudaGetLastError());
 }
 
@@ -838,15 +849,19 @@ swe_status swe_net_check(swe_net *t, void *stream)
     return SWE_OK;
 }
 
-swe_status swe_downsample4(const float *fine, long long f_img, long long f_plane, long long f_pitch, float *coarse,
-                           long long c_img, long long c_plane, long long c_pitch, int Wc, int Hc, int n,
-                           void *stream)
+swe_status swe_downsample(int factor, const float *fine, long long f_img, long long f_plane, long long f_pitch,
+                          float *coarse, long long c_img, long long c_plane, long long c_pitch, int Wc, int Hc, int n,
+                          void *stream)
 {
-    if (!fine || !coarse || Wc < 1 || Hc < 1 || n < 1 || f_pitch < 4 * Wc || c_pitch < Wc) return SWE_EINVAL;
-    if (((uintptr_t)fine % 16) || (f_pitch % 4) || (f_plane % 4) || (f_img % 4)) return SWE_EINVAL;
+    if (!fine || !coarse || Wc < 1 || Hc < 1 || n < 1 || factor < 1 || factor > 4) return SWE_EINVAL;
+    if (f_pitch < (long long)factor * Wc || c_pitch < Wc) return SWE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    downsample4_kernel<<<1184, 256, 0, s>>>(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc,
-                                            n);
+    switch (factor) {
+        case 1: downsample_kernel<1><<<1184, 256, 0, s>>>(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n); break;
+        case 2: downsample_kernel<2><<<1184, 256, 0, s>>>(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n); break;
+        case 3: downsample_kernel<3><<<1184, 256, 0, s>>>(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n); break;
+        default: downsample_kernel<4><<<1184, 256, 0, s>>>(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n); break;
+    }
     return nst(cudaGetLastError());
 }
 

@@ -74,20 +74,21 @@ _SIGS = {
     "swe_batch_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_selftest_wait": (_i, [_i, _d, _vp]),
     "swe_batch_state_ptr": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "swe_batch_copy_states": (_i, [_vp, _vp, _vp]),
     "swe_net_param_count": (ctypes.c_size_t, []),
     "swe_net_create": (_i, [_i, _i, _i, ctypes.POINTER(_vp)]),
     "swe_net_destroy": (None, [_vp]),
     "swe_net_set_params": (_i, [_vp, _vp]),
     "swe_net_get_params": (_i, [_vp, _vp]),
     "swe_net_set_norm": (_i, [_vp, _vp]),
-    "swe_net_prep_input": (_i, [_vp, _i, _vp, _ll, _ll, _ll, _vp]),
+    "swe_net_prep_input": (_i, [_vp, _i, _vp, _vp, _ll, _ll, _ll, _vp]),
     "swe_net_infer": (_i, [_vp, _i, _vp, _vp]),
     "swe_net_apply": (_i, [_vp, _i, _vp, _ll, _ll, _ll, _i, _vp]),
-    "swe_net_make_target": (_i, [_vp, _i, _vp, _vp, _ll, _ll, _ll, _vp, _vp]),
+    "swe_net_make_target": (_i, [_vp, _i, _vp, _vp, _ll, _ll, _ll, ctypes.c_float, _vp, _vp]),
     "swe_net_train_step": (_i, [_vp, _i, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i,
                                 ctypes.POINTER(_d), _vp, _vp, _vp]),
     "swe_net_check": (_i, [_vp, _vp]),
-    "swe_downsample4": (_i, [_vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
+    "swe_downsample": (_i, [_i, _vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
 
 
@@ -386,6 +387,11 @@ class Batch:
         check(lib().swe_batch_query(self.b, int(key), ctypes.byref(v)), "swe_batch_query")
         return v.value
 
+    def copy_states(self, dst_ptr, stream=None):
+        """All current states into a contiguous device buffer [n][3][ny][nx]."""
+        check(lib().swe_batch_copy_states(self.b, dst_ptr, stream if stream is not None else current_stream()),
+              "swe_batch_copy_states")
+
     def state_ptr(self, i):
         """(device address of instance i's h plane, plane stride, pitch)."""
         p, ps, pi = _vp(), _ll(), _ll()
@@ -455,8 +461,8 @@ class Net:
         a = np.array([h0, sh, su, oh, ou], np.float32)
         check(lib().swe_net_set_norm(self.t, a.ctypes.data), "swe_net_set_norm")
 
-    def prep_input(self, n, state_ptr, img_stride, plane_stride, pitch, stream=None):
-        check(lib().swe_net_prep_input(self.t, n, state_ptr, img_stride, plane_stride, pitch,
+    def prep_input(self, n, state_ptr, img_stride, plane_stride, pitch, base_ptr=None, stream=None):
+        check(lib().swe_net_prep_input(self.t, n, state_ptr, base_ptr, img_stride, plane_stride, pitch,
                                        stream if stream is not None else current_stream()), "swe_net_prep_input")
 
     def infer(self, n, resid_ptr=None, stream=None):
@@ -467,9 +473,10 @@ class Net:
         check(lib().swe_net_apply(self.t, n, state_ptr, img_stride, plane_stride, pitch, int(project_mass),
                                   stream if stream is not None else current_stream()), "swe_net_apply")
 
-    def make_target(self, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, target_ptr, stream=None):
-        check(lib().swe_net_make_target(self.t, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, target_ptr,
-                                        stream if stream is not None else current_stream()), "swe_net_make_target")
+    def make_target(self, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, target_ptr, clip=0.0, stream=None):
+        check(lib().swe_net_make_target(self.t, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, clip,
+                                        target_ptr, stream if stream is not None else current_stream()),
+              "swe_net_make_target")
 
     def train_step(self, n, target_ptr, lr=1e-3, wd=0.0, clip=0.0, update=True, want_grads=False,
                    resid_ptr=None, stream=None):
@@ -484,6 +491,6 @@ class Net:
         return int(lib().swe_net_check(self.t, stream if stream is not None else current_stream()))
 
 
-def swe_downsample4(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n, stream=None):
-    check(lib().swe_downsample4(fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n,
-                                stream if stream is not None else current_stream()), "swe_downsample4")
+def swe_downsample(factor, fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n, stream=None):
+    check(lib().swe_downsample(int(factor), fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc,
+                               n, stream if stream is not None else current_stream()), "swe_downsample")

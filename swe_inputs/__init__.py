@@ -225,3 +225,9 @@ def smooth_flow_state(seed: int, nx: int, ny: int, amp_u: float = 0.3) -> State:
     hu = amp_u * h * (np.cos(math.pi * a * y)[:, None] * np.cos(0.7 * math.pi * x)[None, :])
     hv = amp_u * h * (np.sin(0.9 * math.pi * y)[:, None] * np.cos(math.pi * b * x)[None, :])
     return State(h, hu, hv)
+
+
+def corrector_states(seeds, n: int = 1024, dam_fraction: float = 0.1) -> List[State]:
+    """Initial fine states of the corrector's training / evaluation
+    trajectories (one per seed)."""
+    return [corrector_training_state(s, n, dam_fraction) for s in seeds]

@@ -71,7 +71,7 @@ def test_forward_matches_oracle(n, H, W):
     dev = torch.from_numpy(st).cuda()
     resid = torch.zeros((n, 3, H, W), dtype=torch.float32, device="cuda")
     with _net_with(params, n, H, W) as net:
-        net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)
+        net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)  # state mode (no base)
         net.infer(n, resid.data_ptr())
         assert net.check() == 0
     got = resid.cpu().numpy()
@@ -93,7 +93,7 @@ def test_backward_matches_oracle():
     r_dev = torch.zeros((n, 3, H, W), dtype=torch.float32, device="cuda")
     from paper_1107_2157_gb300 import swe
     with _net_with(params, n, H, W) as net:
-        net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)
+        net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)  # state mode (no base)
         loss, g = net.train_step(n, tdev.data_ptr(), update=False, want_grads=True, resid_ptr=r_dev.data_ptr())
     op = _oracle_params(params)
     r, cache = nn.forward(op, _oracle_inputs(st))
@@ -107,18 +107,19 @@ def test_backward_matches_oracle():
         assert cosine(gg[k], grads[k]) >= 0.999, (k, cosine(gg[k], grads[k]))
 
 
-def test_downsample4_matches_oracle():
+@pytest.mark.parametrize("factor", [2, 3, 4])
+def test_block_average_matches_oracle(factor):
     import torch
     from paper_1107_2157_gb300 import swe
-    n, Hc, Wc = 3, 12, 20
+    n, Hc, Wc, F = 3, 12, 20, factor
     rng = np.random.default_rng(4)
-    fine = rng.standard_normal((n, 3, 4 * Hc, 4 * Wc)).astype(np.float32)
+    fine = rng.standard_normal((n, 3, F * Hc, F * Wc)).astype(np.float32)
     fdev = torch.from_numpy(fine).cuda()
     cdev = torch.zeros((n, 3, Hc, Wc), dtype=torch.float32, device="cuda")
-    swe.swe_downsample4(fdev.data_ptr(), 3 * 16 * Hc * Wc, 16 * Hc * Wc, 4 * Wc, cdev.data_ptr(),
-                        3 * Hc * Wc, Hc * Wc, Wc, Wc, Hc, n)
+    swe.swe_downsample(F, fdev.data_ptr(), 3 * F * F * Hc * Wc, F * F * Hc * Wc, F * Wc, cdev.data_ptr(),
+                       3 * Hc * Wc, Hc * Wc, Wc, Wc, Hc, n)
     torch.cuda.synchronize()
-    ref = nn.downsample4(fine.astype(np.float64))
+    ref = nn.block_average(fine.astype(np.float64), F)
     assert np.abs(cdev.cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
 
 
@@ -133,7 +134,7 @@ def test_training_reduces_the_loss_on_a_fixed_batch():
     dev = torch.from_numpy(st).cuda()
     tdev = torch.from_numpy(np.ascontiguousarray(target)).cuda()
     with _net_with(params, n, H, W) as net:
-        net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)
+        net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)  # state mode (no base)
         first, _ = net.train_step(n, tdev.data_ptr(), lr=3e-3)
         for _ in range(300):
             last, _ = net.train_step(n, tdev.data_ptr(), lr=3e-3)
