@@ -44,8 +44,13 @@ def parse():
     p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="grid", choices=["grid", "ensemble"],
-                   help="grid: one 8192^2 grid (default); ensemble: 512 uneven grids in one persistent launch")
+    p.add_argument("--workload", default="grid", choices=["grid", "ensemble", "learned"],
+                   help="grid: one 8192^2 grid (default); ensemble: 512 uneven grids in one persistent launch; "
+                        "learned: train the corrector and compare learned-coarse serving with plain fine runs")
+    p.add_argument("--train-trajectories", type=int, default=1792)
+    p.add_argument("--eval-trajectories", type=int, default=200)
+    p.add_argument("--serve-instances", type=int, default=1024)
+    p.add_argument("--passes", type=int, default=1)
     p.add_argument("--tune-cache", default=None)
     return p.parse_args()
 
@@ -432,12 +437,113 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# learned workload: train the corrector, then learned-coarse vs plain fine
+# ---------------------------------------------------------------------------
+
+def run_learned(args):
+    import numpy as np
+    import torch
+
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import corrector as C
+    from paper_1107_2157_gb300 import swe
+
+    torch.cuda.set_device(0)
+    sp = torch.cuda.current_stream().cuda_stream
+    setup = C.Setup(n_fine=1024, factor=4, dt_fine=0.04, coarse_steps=64)
+    nc = setup.n_coarse
+    t0 = time.perf_counter()
+    res = C.train(setup, range(0, args.train_trajectories), B=32, lr=1e-3, passes=args.passes, gen_batch=64)
+    t_train = time.perf_counter() - t0
+
+    def restrict(batch, factor, n):
+        out = torch.zeros((n, 3, nc, nc), dtype=torch.float32, device="cuda")
+        p0, plane, pitch = batch.state_ptr(0)
+        img = (batch.state_ptr(1)[0] - p0) // 4 if n > 1 else 3 * plane
+        swe.swe_downsample(factor, p0, img, plane, pitch, out.data_ptr(), 3 * nc * nc, nc * nc, nc, nc, nc, n)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    # held-out error of config "training": seeds 1800.., 64 coarse steps
+    eval_seeds = list(range(1800, 1800 + args.eval_trajectories))
+    e_plain, e_learned, flags_eval = [], [], 0
+    for c in range(0, len(eval_seeds), 100):
+        st = si.corrector_states(eval_seeds[c:c + 100], setup.n_fine, setup.dam_fraction)
+        truth = C.fine_truth(setup, st)
+        b = C.coarse_run(setup, st, None, None)
+        e_plain += list(C.rms_h_error(b, truth))
+        b.close()
+        out = C.serve(setup, st, res["params"], res["norm"])
+        e_learned += list(C.rms_h_error(out["coarse"], truth))
+        flags_eval += int(out["flagged"].sum())
+        out["coarse"].close()
+    e_plain, e_learned = np.array(e_plain), np.array(e_learned)
+
+    # serving: N instances (seeds 10000..) learned-coarse vs plain fine and plain 512^2
+    n = args.serve_instances
+    states = si.corrector_states(range(10000, 10000 + n), setup.n_fine, setup.dam_fraction)
+    out = C.serve(setup, states, res["params"], res["norm"])  # warm-up / compile
+    out["coarse"].close()
+    out = C.serve(setup, states, res["params"], res["norm"])
+    t_learned = out["seconds"]
+    fallback_rate = float(out["flagged"].mean())
+    learned_c = out["coarse"]
+    tt = []
+    truth = C.fine_truth(setup, states, timing=tt)
+    t_fine = tt[0]
+    el = C.rms_h_error(learned_c, truth)
+    learned_c.close()
+    # plain coarse 256^2 and plain 512^2 on the same initial states
+    tp = []
+    pc = C.coarse_run(setup, states, None, None, timing=tp)
+    ep256 = C.rms_h_error(pc, truth)
+    pc.close()
+    setup512 = C.Setup(n_fine=1024, factor=2, dt_fine=0.04, coarse_steps=128)
+    tp512 = []
+    b512 = C.coarse_run(setup512, states, None, None, timing=tp512)
+    r512 = restrict(b512, 2, n)
+    b512.close()
+    ep512 = np.sqrt(((r512[:, 0].astype(np.float64) - truth[:, 0]) ** 2).mean(axis=(1, 2)))
+    levels = [(256, float(ep256.mean()), tp[0]), (512, float(ep512.mean()), tp512[0]), (1024, 0.0, t_fine)]
+    l_err = float(el.mean())
+    n_star = next(N for N, e, _ in levels if e <= l_err)
+    t_star = next(t for N, e, t in levels if N == n_star)
+    fine_updates = n * 1024 * 1024 * 256
+    line = {
+        "metric": METRIC, "workload": "learned", "unit": "s",
+        "train": {"trajectories": args.train_trajectories, "steps": res["steps"], "seconds": t_train,
+                  "loss_first": float(np.mean(res["losses"][:50])), "loss_last": float(np.mean(res["losses"][-200:])),
+                  "norm": res["norm"]},
+        "eval_training_config": {"seeds": "1800..%d" % (1799 + args.eval_trajectories),
+                                 "l2_h_plain_coarse_mean": float(e_plain.mean()),
+                                 "l2_h_learned_mean": float(e_learned.mean()),
+                                 "l2_h_plain_coarse_median": float(np.median(e_plain)),
+                                 "l2_h_learned_median": float(np.median(e_learned)),
+                                 "median_ratio": float(np.median(e_learned / e_plain)),
+                                 "fallbacks": flags_eval},
+        "serving": {"instances": n, "coarse": "256x256", "coarse_steps": 64,
+                    "t_learned_s": t_learned, "t_plain_fine_1024_s": t_fine, "t_plain_512_s": tp512[0],
+                    "t_plain_coarse_256_s": tp[0],
+                    "l2_h_learned_mean": l_err, "l2_h_plain_256_mean": levels[0][1],
+                    "l2_h_plain_512_mean": levels[1][1], "l2_h_learned_median": float(np.median(el)),
+                    "l2_h_plain_256_median": float(np.median(ep256)), "l2_h_plain_512_median": float(np.median(ep512)),
+                    "equal_error_N": n_star, "speedup_vs_plain_fine_1024": t_fine / t_learned,
+                    "speedup_vs_plain_at_equal_error": t_star / t_learned, "fallback_rate": fallback_rate,
+                    "coarse_cell_updates_per_s": n * nc * nc * 64 / t_learned,
+                    "fine_equivalent_cell_updates_per_s": fine_updates / t_learned},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:
