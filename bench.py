@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
+    p.add_argument("--variant", type=int, default=None, help="two-step kernel tile shape 0..3 (with --kernel 3)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="grid", choices=["grid", "ensemble", "learned"],
                    help="grid: one 8192^2 grid (default); ensemble: 512 uneven grids in one persistent launch; "
@@ -74,6 +75,24 @@ def workload_config(n, steps):
     }
 
 
+def aggregate_over_ranks(times, world_size, device=None):
+    """Max over ranks of each timing in ``times`` (job, steps, e2e ...): the
+    slowest rank sets the whole job's time.  Uses the initialised process
+    group (NCCL on GPUs, gloo in the CPU tests); a single rank returns its own."""
+    import torch
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world_size, cells_per_rank, steps, t_max):
+    """Cell-updates per second of all ranks together (replicas: every rank
+    advances its own grid of ``cells_per_rank`` cells by ``steps`` steps)."""
+    return world_size * cells_per_rank * steps / t_max
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -86,7 +105,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1107_2157_gb300/csrc/swe_step.cu", "paper_1107_2157_gb300/csrc/swe_device.cuh"):
+    for rel in ("paper_1107_2157_gb300/csrc/swe_step.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
+                "paper_1107_2157_gb300/csrc/swe_device.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -270,7 +290,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    grid = Grid(n, n, 1.0, 1.0, 0.01, G, dtype="f32", kernel=args.kernel)
+    grid = Grid(n, n, 1.0, 1.0, 0.01, G, dtype="f32", kernel=args.kernel, variant=args.variant)
 
     def barrier():
         if ws > 1:
@@ -331,16 +351,12 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
 
     # max over ranks
-    times = torch.tensor([t_job, t_steps, t_e2e], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    t_job, t_steps, t_e2e = (float(x) for x in times.tolist())
+    t_job, t_steps, t_e2e = aggregate_over_ranks([t_job, t_steps, t_e2e], ws, device="cuda")
     grid.close()
     if rank != 0:
         return
 
-    value = ws * cells * args.steps / t_job
+    value = whole_job_rate(ws, cells, args.steps, t_job)
     per_launch = t_steps / max(1, launches)
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_CELL_F32 * cells / per_launch / 1e9
@@ -359,7 +375,7 @@ def run_ours(args):
                      "kernel": "lw_tiled_kernel<float> (one launch per step)",
                      "algorithmic_bytes_per_launch": BYTES_PER_CELL_F32 * cells,
                      "launch_ms": per_launch * 1e3, "peak_source": peak_kind + " hbm_gbs (copy)"},
-        "e2e": {"value": ws * cells * args.steps / t_e2e, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(ws, cells, args.steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * 4 * cells / args.steps, "d2h_bytes_per_step": 3 * 4 * cells / args.steps,
                 "note": "the job through the C ABI from pinned host buffers: host->device state (3 x FP32 "
                         "planes), FP64 CFL dt, K steps, FP64 mass, device->host state; the state crosses "

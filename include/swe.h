@@ -56,14 +56,15 @@ typedef enum {
     SWE_KERNEL_AUTO = 0,   /* the fastest variant for the dtype and size */
     SWE_KERNEL_NAIVE = 1,  /* one thread per cell, neighbours from global memory */
     SWE_KERNEL_TILED = 2,  /* TMA tile + halo in shared memory, one step per launch */
-    SWE_KERNEL_TEMPORAL = 3 /* TMA tile + k-cell halo, k steps per launch */
+    SWE_KERNEL_TEMPORAL = 3 /* TMA tile + 2-cell halo, 2 steps per launch (an odd
+                               last step uses the one-step kernel); same bits */
 } swe_kernel;
 
 typedef struct {
     int dtype;   /* swe_dtype; default SWE_F32 */
     int kernel;  /* swe_kernel; default SWE_KERNEL_AUTO */
-    int depth;   /* steps per launch for SWE_KERNEL_TEMPORAL; 0 = default */
-    int reserved[5];
+    int depth;   /* 0 = default; SWE_KERNEL_TEMPORAL runs 2 steps per launch */
+    int reserved[5]; /* reserved[0]: two-step tile shape + 1 (0 = default shape 1 of 0..3); others 0 */
 } swe_options;
 
 /* Fills *opt with the defaults (FP32, automatic kernel choice). */
@@ -139,7 +140,8 @@ typedef enum {
     SWE_Q_LAUNCHES = 3,         /* step-kernel launches enqueued so far */
     SWE_Q_TILE_X = 4,           /* tile width in cells */
     SWE_Q_TILE_Y = 5,           /* tile height in cells */
-    SWE_Q_STATE_PTR = 6         /* device address of the current H plane */
+    SWE_Q_STATE_PTR = 6,        /* device address of the current H plane */
+    SWE_Q_STEPS_PER_LAUNCH = 7  /* steps a full step-kernel launch advances */
 } swe_query_key;
 
 /* Writes the value of ``key`` to *value. */
@@ -321,6 +323,12 @@ swe_status swe_net_infer(swe_net *net, int n, float *resid, void *stream);
  * the corrected step keeps the Lax-Wendroff step's mass. */
 swe_status swe_net_apply(swe_net *net, int n, float *state, long long img_stride, long long plane_stride,
                          long long pitch, int project_mass, void *stream);
+/* The corrected step in one call on the prepared input: the network, with
+ * its scaled residual added to ``state`` in the last layer's epilogue;
+ * with project_mass the per-image mean of the h correction is then
+ * subtracted (mass of the Lax-Wendroff step kept up to rounding). */
+swe_status swe_net_correct(swe_net *net, int n, float *state, long long img_stride, long long plane_stride,
+                           long long pitch, int project_mass, void *stream);
 /* Training target (normalised): (next - lw) / (oh, ou, ou), clipped to
  * [-clip, clip] if clip > 0, FP32 [n][3][H][W]; next is FP32 [n][3][H][W]
  * contiguous, lw a state as above. */
@@ -336,6 +344,9 @@ swe_status swe_net_train_step(swe_net *net, int n, const float *target, float lr
                               double *loss_out, float *grads_out, float *resid_out, void *stream);
 /* Synchronises and returns the device error word of the net's kernels. */
 swe_status swe_net_check(swe_net *net, void *stream);
+/* Self-test of the network's activation on the device: out[i] = erf(z[i])
+ * (which = 0), gelu(z[i]) (1) or gelu'(z[i]) (2); device pointers. */
+swe_status swe_selftest_gelu(const float *z, float *out, int n, int which, void *stream);
 /* factor x factor block average (factor 1..4) of n images (3 planes each)
  * of (factor Hc) x (factor Wc) fine cells into Hc x Wc coarse cells; strides
  * in floats as above.  The restriction that turns a fine solution into the

@@ -236,8 +236,7 @@ def coarse_run(setup: Setup, states: List[si.State], params: Optional[np.ndarray
             coarse.step(1, stream=sp)
             l0, limg, lpl, lpi = _Pair.geom(coarse)
             net.prep_input(B, l0, limg, lpl, lpi, base_ptr=c0, stream=sp)
-            net.infer(B, None, stream=sp)
-            net.apply(B, l0, limg, lpl, lpi, project_mass=project_mass, stream=sp)
+            net.correct(B, l0, limg, lpl, lpi, project_mass=project_mass, stream=sp)
     torch.cuda.synchronize()
     if timing is not None:
         timing.append(time.perf_counter() - t0)
@@ -310,8 +309,7 @@ def serve(setup: Setup, states: List[si.State], params: np.ndarray, norm, mass_t
             coarse.step(1, stream=sp)
             l0, limg, lpl, lpi = _Pair.geom(coarse)
             net.prep_input(B, l0, limg, lpl, lpi, base_ptr=c0, stream=sp)
-            net.infer(B, None, stream=sp)
-            net.apply(B, l0, limg, lpl, lpi, project_mass=project_mass, stream=sp)
+            net.correct(B, l0, limg, lpl, lpi, project_mass=project_mass, stream=sp)
         rc, flags = coarse.status(stream=sp)
         m1 = coarse.mass(stream=sp)
         t1 = time.perf_counter()

@@ -22,7 +22,9 @@ struct swe_ctx {
     int cur = 0;            // buffer holding the current state
     int kernel = SWE_KERNEL_AUTO;
     int depth = 1;
-    CUtensorMap maps[2][3];  // TMA maps of both buffers (tiled kernels)
+    int tb_variant = 0;         // two-step kernel shape
+    CUtensorMap maps[2][3];     // TMA maps of both buffers, one-step box
+    CUtensorMap maps_tb[2][3];  // TMA maps of both buffers, two-step box
     double *scratch = nullptr;  // reduction partials (device)
     double *result = nullptr;   // reduction results (device, 4 doubles)
     double *host_result = nullptr;  // pinned copy of result
@@ -152,7 +154,7 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     if (!finite_pos(dx) || !finite_pos(dy) || !finite_pos(dt) || !finite_pos(g)) return SWE_EINVAL;
     if (o.dtype != SWE_F32 && o.dtype != SWE_F64) return SWE_EINVAL;
     if (o.kernel < SWE_KERNEL_AUTO || o.kernel > SWE_KERNEL_TEMPORAL) return SWE_EINVAL;
-    if (o.kernel == SWE_KERNEL_TEMPORAL) return SWE_EUNSUPPORTED;
+    if (o.depth < 0 || o.depth > 2) return SWE_EUNSUPPORTED;
 
     swe_ctx *c = new (std::nothrow) swe_ctx();
     if (!c) return SWE_ENOMEM;
@@ -168,7 +170,8 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     c->pitch = plane_pitch(nx, c->esize);
     c->plane = (size_t)c->pitch * (size_t)ny;
     c->kernel = o.kernel == SWE_KERNEL_AUTO ? SWE_KERNEL_TILED : o.kernel;
-    c->depth = 1;
+    c->depth = c->kernel == SWE_KERNEL_TEMPORAL ? 2 : 1;
+    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 4) ? o.reserved[0] - 1 : 1;
 
     const size_t bytes = 3 * c->plane * c->esize;
     swe_status st = SWE_OK;
@@ -188,13 +191,17 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     if ((st = cuda_status(cudaMemset(c->err, 0, sizeof(int)))) != SWE_OK) return fail(st);
     if ((st = cuda_status(cudaMallocHost(&c->host_result, 4 * sizeof(double)))) != SWE_OK) return fail(st);
 
-    if (c->kernel == SWE_KERNEL_TILED) {
-        int bw, bh;
+    if (c->kernel == SWE_KERNEL_TILED || c->kernel == SWE_KERNEL_TEMPORAL) {
+        int bw, bh, tw, th;
         tiled_box(c->dtype, &bw, &bh);
+        tb2_box(c->dtype, c->tb_variant, &tw, &th);
         for (int b = 0; b < 2; ++b)
-            for (int k = 0; k < 3; ++k)
+            for (int k = 0; k < 3; ++k) {
                 if (!encode_plane_map(&c->maps[b][k], c->dtype, plane_ptr(c, b, k), nx, ny, c->pitch, bw, bh))
                     return fail(SWE_ECUDA);
+                if (!encode_plane_map(&c->maps_tb[b][k], c->dtype, plane_ptr(c, b, k), nx, ny, c->pitch, tw, th))
+                    return fail(SWE_ECUDA);
+            }
     }
     *out = c;
     return SWE_OK;
@@ -251,7 +258,18 @@ swe_status swe_step(swe_ctx *c, int n_steps, void *stream)
 {
     if (!c || n_steps < 0) return SWE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (int n = 0; n < n_steps; ++n) {
+    int n = 0;
+    if (c->kernel == SWE_KERNEL_TEMPORAL) {
+        for (; n + 2 <= n_steps; n += 2) {
+            const int in = c->cur, outb = c->cur ^ 1;
+            cudaError_t e = launch_tb2(c->dtype, c->tb_variant, c->maps_tb[in], c->state[outb], c->plane, c->nx,
+                                       c->ny, c->pitch, c->dx, c->dy, c->dt, c->g, c->err, s);
+            if (e != cudaSuccess) return cuda_status(e);
+            c->cur = outb;
+            c->launches += 1;
+        }
+    }
+    for (; n < n_steps; ++n) {
         const int in = c->cur, outb = c->cur ^ 1;
         cudaError_t e;
         if (c->kernel == SWE_KERNEL_NAIVE)
@@ -319,6 +337,7 @@ swe_status swe_query(swe_ctx *c, int key, long long *value)
         case SWE_Q_PITCH: *value = c->pitch; break;
         case SWE_Q_LAUNCHES: *value = c->launches; break;
         case SWE_Q_TILE_X: *value = c->kernel == SWE_KERNEL_NAIVE ? 64 : tiled_geom(c->dtype).tile_x; break;
+        case SWE_Q_STEPS_PER_LAUNCH: *value = c->depth; break;
         case SWE_Q_TILE_Y: *value = c->kernel == SWE_KERNEL_NAIVE ? 4 : tiled_geom(c->dtype).tile_y; break;
         case SWE_Q_STATE_PTR: *value = (long long)(uintptr_t)plane_ptr(c, c->cur, 0); break;
         default: return SWE_EINVAL;

@@ -34,6 +34,9 @@ cudaError_t launch_naive(int dtype, const void *in, void *out, size_t plane, int
                          double dx, double dy, double dt, double g, cudaStream_t s);
 cudaError_t launch_tiled(int dtype, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
                          long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+cudaError_t launch_tb2(int dtype, int variant, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
+                       long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+void tb2_box(int dtype, int variant, int *bw, int *bh);  // TMA box of two-step kernel shape ``variant``
 StepGeom tiled_geom(int dtype);
 void tiled_box(int dtype, int *bw, int *bh);  // TMA box the tiled kernel loads
 

@@ -39,7 +39,10 @@ constexpr int kTileX = 128;                // output pixels per tile row (the MM
 constexpr int kHaloX = kTileX + 2;         // 130
 constexpr int kPixB = 16;                  // bytes per pixel strip (8 bf16)
 constexpr int kStripB = kHaloX * kPixB;    // 2080: one channel strip of the halo tile
-constexpr int kConvRows = 4;               // output rows per CTA
+#ifndef SWE_CONV_ROWS
+#define SWE_CONV_ROWS 4
+#endif
+constexpr int kConvRows = SWE_CONV_ROWS;   // output rows per CTA
 
 __host__ __device__ constexpr size_t al128(size_t x) { return (x + 127) / 128 * 128; }
 __host__ __device__ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
@@ -58,17 +61,11 @@ struct ConvCfg {
     static constexpr size_t OFF_B = al128(A_BYTES);
     static constexpr size_t OFF_BAR = al128(OFF_B + B_BYTES);
     static constexpr size_t USED = OFF_BAR + 64;
-    // The smem allocation also covers every byte the MMAs could address if
-    // the roles of the two descriptor strides were the other way round, so
-    // a layout mistake cannot reach outside the CTA's shared memory.
-    static constexpr size_t A_ALT_END =
-        ((size_t)(R + 1) * CH + 2 * (NKS - 1)) * kStripB + 2 * kPixB + 15 * kStripB + 2 * 128;
-    static constexpr size_t B_ALT_END = OFF_B + (9 * NKS - 1) * B_BLOCK + (NC - 1) * NC * 128 + 2 * 128;
-    static constexpr size_t SMEM = cmax(USED, cmax(A_ALT_END, B_ALT_END)) + 128;
+    static constexpr size_t SMEM = USED + 128;
     static constexpr uint32_t TMEM_COLS = pow2_at_least((uint32_t)(R * COUT));
 };
 
-enum { EPI_GELU = 0, EPI_GELU_BWD = 1, EPI_LOSS = 2, EPI_RESID = 3 };
+enum { EPI_GELU = 0, EPI_GELU_BWD = 1, EPI_LOSS = 2, EPI_RESID = 3, EPI_APPLY = 4 };
 
 struct EpiArgs {
     const float *bias;        // COUT floats (EPI_GELU, EPI_LOSS, EPI_RESID)
@@ -77,7 +74,10 @@ struct EpiArgs {
     const bf16 *zin;          // EPI_GELU_BWD: pre-activation of the layer being differentiated
     const float *target;      // EPI_LOSS: FP32 [n][3][H][W] normalised targets
     float *resid;             // EPI_RESID: FP32 [n][3][H][W] output (scaled); EPI_LOSS: optional r
-    float oscale[3];          // EPI_RESID: per-channel output scale
+    float oscale[3];          // EPI_RESID / EPI_APPLY: per-channel output scale
+    float *state;             // EPI_APPLY: state planes the scaled residual is added to
+    long long st_img, st_plane, st_pitch;  // EPI_APPLY: their strides (floats)
+    double *hsum;             // EPI_APPLY: per-image sum of the h correction (may be null)
     float loss_scale;         // EPI_LOSS: d loss / d r factor (2 / count)
     double *loss_accum;       // EPI_LOSS: sum of squared errors
 };
@@ -92,11 +92,45 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.26:
+// erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
+// t = 1 / (1 + p x) for x >= 0 (odd extension), |error| <= 1.5e-7.  Also
+// returns exp(-x^2), which the GELU derivative reuses.
+__device__ __forceinline__ float erf_as(float x, float &gauss)
+{
+    const float ax = fabsf(x);
+    const float t = rcp(fmaf(0.3275911f, ax, 1.0f));
+    float poly = fmaf(1.061405429f, t, -1.453152027f);
+    poly = fmaf(poly, t, 1.421413741f);
+    poly = fmaf(poly, t, -0.284496736f);
+    poly = fmaf(poly, t, 0.254829592f);
+    poly *= t;
+    gauss = __expf(-ax * ax);
+    const float e = fmaf(-poly, gauss, 1.0f);
+    return copysignf(e, x);
+}
+
+// GELU 0.5 z (1 + erf(z / sqrt 2)) and its derivative 0.5 (1 + erf(z / sqrt 2)) + z phi(z).
+__device__ __forceinline__ float gelu_f(float z)
+{
+    float g;
+    return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f, g));
+}
 
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    float g;  // exp(-z^2 / 2)
+    const float e = erf_as(z * 0.70710678118654752f, g);
+    return fmaf(z * g, 0.39894228040143268f, 0.5f * (1.0f + e));
+}
+
+// Evaluates erf (which = 0), gelu (1) or gelu' (2) of n values (self-test).
+__global__ void gelu_probe_kernel(const float *__restrict__ z, float *__restrict__ out, int n, int which)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float g;
+        out[i] = which == 0 ? erf_as(z[i], g) : (which == 1 ? gelu_f(z[i]) : gelu_grad_f(z[i]));
+    }
 }
 
 __device__ __forceinline__ size_t rc_index(int n, int y, int c, int x, int H, int W, int CHO)
@@ -138,6 +172,34 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
 
+    // Epilogue operands that do not depend on the MMA are fetched now, so
+    // their latency overlaps the loads and the MMAs.
+    const int px = x0 + warp * 32 + lane;
+    constexpr int PF = (EPI == EPI_GELU_BWD) ? COUT / 8 : ((EPI == EPI_LOSS || EPI == EPI_APPLY) ? 3 : 1);
+    uint4 zpre[R][EPI == EPI_GELU_BWD ? PF : 1];
+    float fpre[R][(EPI == EPI_LOSS || EPI == EPI_APPLY) ? 3 : 1];
+    if (px < W) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = y0 + r;
+            if (y >= H) break;
+            if constexpr (EPI == EPI_GELU_BWD) {
+#pragma unroll
+                for (int c = 0; c < PF; ++c)
+                    zpre[r][c] = *reinterpret_cast<const uint4 *>(ea.zin + rc_index(n, y, c, px, H, W, PF));
+            } else if constexpr (EPI == EPI_LOSS) {
+                const size_t plane = (size_t)H * W;
+                const size_t po = ((size_t)n * 3) * plane + (size_t)y * W + px;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fpre[r][c] = __ldg(ea.target + po + c * plane);
+            } else if constexpr (EPI == EPI_APPLY) {
+                const float *st = ea.state + n * ea.st_img + (long long)y * ea.st_pitch + px;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) fpre[r][c] = st[c * ea.st_plane];
+            }
+        }
+    }
+
     bool ok = __syncthreads_and(mbar_wait_bounded(bar_tma, 0, err));
     if (ok && tid == 0) {
         constexpr uint32_t idesc = tc::idesc_bf16(128, COUT);
@@ -165,7 +227,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
         const int x = x0 + warp * 32 + lane;
         const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
         double lsum = 0.0;
-#pragma unroll 1
+#pragma unroll
         for (int r = 0; r < R; ++r) {
             const int y = y0 + r;
             float v[COUT];
@@ -190,7 +252,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                         *reinterpret_cast<uint4 *>(ea.out + o) = *reinterpret_cast<const uint4 *>(a8);
                         if (ea.zout) *reinterpret_cast<uint4 *>(ea.zout + o) = *reinterpret_cast<const uint4 *>(z8);
                     } else {
-                        const uint4 zr = *reinterpret_cast<const uint4 *>(ea.zin + o);
+                        const uint4 zr = zpre[r][c];
                         const bf16 *zz = reinterpret_cast<const bf16 *>(&zr);
 #pragma unroll
                         for (int k = 0; k < 8; ++k)
@@ -210,7 +272,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                     for (int k = 0; k < 16; ++k) d8[k] = __float2bfloat16_rn(0.0f);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float d = rr[c] - __ldg(ea.target + po + c * plane);
+                        const float d = rr[c] - fpre[r][c];
                         lsum += (double)d * (double)d;
                         d8[c] = __float2bfloat16_rn(ea.loss_scale * d);
                         if (ea.resid) ea.resid[po + c * plane] = rr[c];
@@ -219,16 +281,22 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                         *reinterpret_cast<const uint4 *>(d8);
                     *reinterpret_cast<uint4 *>(ea.out + rc_index(n, y, 1, x, H, W, 2)) =
                         *reinterpret_cast<const uint4 *>(d8 + 8);
-                } else {
+                } else if constexpr (EPI == EPI_RESID) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) ea.resid[po + c * plane] = rr[c] * ea.oscale[c];
+                } else {
+                    float *st = ea.state + n * ea.st_img + (long long)y * ea.st_pitch + x;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) st[c * ea.st_plane] = fpre[r][c] + rr[c] * ea.oscale[c];
+                    lsum += (double)(rr[0] * ea.oscale[0]);
                 }
             }
         }
-        if constexpr (EPI == EPI_LOSS) {
+        if constexpr (EPI == EPI_LOSS || EPI == EPI_APPLY) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-            if (lane == 0 && lsum != 0.0) atomicAdd(ea.loss_accum, lsum);
+            double *acc = EPI == EPI_LOSS ? ea.loss_accum : (ea.hsum ? ea.hsum + n : nullptr);
+            if (lane == 0 && acc && lsum != 0.0) atomicAdd(acc, lsum);
         }
     }
     tc::fence_before_sync();
@@ -494,6 +562,21 @@ __global__ void __launch_bounds__(1024) apply_correction_kernel(float *__restric
     }
 }
 
+// h[n] -= hsum[n] / (H W) over every cell of each image.
+__global__ void subtract_mean_kernel(float *__restrict__ state, long long img_stride, long long pitch, int W, int H,
+                                     int n, const double *__restrict__ hsum)
+{
+    const long long plane = (long long)H * W;
+    const long long total = (long long)n * plane;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / plane);
+        const long long p = e % plane;
+        const float mean = (float)(hsum[i] / (double)plane);
+        state[i * img_stride + (p / W) * pitch + (p % W)] -= mean;
+    }
+}
+
 // target[n][c][y][x] = (next[n][c][y][x] - lw_c(y, x)) * inv_scale[c], clipped
 // to [-clip, clip] when clip > 0.
 __global__ void make_target_kernel(const float *__restrict__ next, const float *__restrict__ lw, long long img_stride,
@@ -587,6 +670,7 @@ struct swe_net {
     CUtensorMap m_x0, m_a1, m_a2, m_dr, m_dz2;
     float norm[5] = {1.0f, 1.0f, 1.0f, 1.0f, 1.0f};  // h0, sh, su, oh, ou
     double *loss = nullptr, *h_loss = nullptr;
+    double *hsum = nullptr;
     int *err = nullptr;
     long long step = 0;
 };
@@ -627,7 +711,7 @@ void swe_net_destroy(swe_net *t)
                     (void *)t->partial, (void *)t->bias_pad, (void *)t->gnorm, (void *)t->w1f, (void *)t->w2f,
                     (void *)t->w3f, (void *)t->w2d, (void *)t->w3d, (void *)t->x0, (void *)t->z1, (void *)t->a1,
                     (void *)t->z2, (void *)t->a2, (void *)t->dr, (void *)t->dz2, (void *)t->dz1, (void *)t->resid,
-                    (void *)t->loss, (void *)t->err})
+                    (void *)t->loss, (void *)t->err, (void *)t->hsum})
         cudaFree(p);
     cudaFreeHost(t->h_loss);
     delete t;
@@ -661,7 +745,7 @@ swe_status swe_net_create(int max_images, int H, int W, swe_net **out)
         {(void **)&t->x0, px * 16 * 2}, {(void **)&t->z1, px * 32 * 2}, {(void **)&t->a1, px * 32 * 2},
         {(void **)&t->z2, px * 32 * 2}, {(void **)&t->a2, px * 32 * 2}, {(void **)&t->dr, px * 16 * 2},
         {(void **)&t->dz2, px * 32 * 2}, {(void **)&t->dz1, px * 32 * 2}, {(void **)&t->resid, px * 3 * 4},
-        {(void **)&t->loss, 16}, {(void **)&t->err, 16},
+        {(void **)&t->loss, 16}, {(void **)&t->err, 16}, {(void **)&t->hsum, (size_t)max_images * 8},
     };
     for (auto &a : allocs) {
         swe_status st = nst(cudaMalloc(a.p, a.bytes));
@@ -747,6 +831,32 @@ swe_status swe_net_infer(swe_net *t, int n, float *resid_out, void *stream)
     e3.oscale[1] = t->norm[4];
     e3.oscale[2] = t->norm[4];
     N_TRY((launch_conv<4, 16, EPI_RESID>(t->m_a2, t->w3f, e3, t->W, t->H, n, t->err, s)));
+    return SWE_OK;
+}
+
+swe_status swe_net_correct(swe_net *t, int n, float *state, long long img_stride, long long plane_stride,
+                           long long pitch, int project_mass, void *stream)
+{
+    if (!t || !state || n < 1 || n > t->max_n || pitch < t->W) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    swe_status st = forward_hidden(t, n, false, s);
+    if (st != SWE_OK) return st;
+    if (project_mass) N_TRY(cudaMemsetAsync(t->hsum, 0, (size_t)n * sizeof(double), s));
+    EpiArgs e3 = {};
+    e3.bias = t->bias_pad + 64;
+    e3.oscale[0] = t->norm[3];
+    e3.oscale[1] = t->norm[4];
+    e3.oscale[2] = t->norm[4];
+    e3.state = state;
+    e3.st_img = img_stride;
+    e3.st_plane = plane_stride;
+    e3.st_pitch = pitch;
+    e3.hsum = project_mass ? t->hsum : nullptr;
+    N_TRY((launch_conv<4, 16, EPI_APPLY>(t->m_a2, t->w3f, e3, t->W, t->H, n, t->err, s)));
+    if (project_mass) {
+        subtract_mean_kernel<<<1184, 256, 0, s>>>(state, img_stride, pitch, t->W, t->H, n, t->hsum);
+        N_TRY(cudaGetLastError());
+    }
     return SWE_OK;
 }
 
@@ -847,6 +957,14 @@ swe_status swe_net_check(swe_net *t, void *stream)
         return (swe_status)word;
     }
     return SWE_OK;
+}
+
+swe_status swe_selftest_gelu(const float *z, float *out, int n, int which, void *stream)
+{
+    if (!z || !out || n < 0 || which < 0 || which > 2) return SWE_EINVAL;
+    gelu_probe_kernel<<<(n + 255) / 256 > 0 ? std::min((n + 255) / 256, 4096) : 1, 256, 0,
+                        static_cast<cudaStream_t>(stream)>>>(z, out, n, which);
+    return nst(cudaGetLastError());
 }
 
 swe_status swe_downsample(int factor, const float *fine, long long f_img, long long f_plane, long long f_pitch,

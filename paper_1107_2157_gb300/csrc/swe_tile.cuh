@@ -55,44 +55,39 @@ __device__ __forceinline__ void store_vec(T *dst, const T (&x)[VX])
     *reinterpret_cast<V *>(dst) = *reinterpret_cast<const V *>(x);
 }
 
-// Computes one output tile from the staged box (see TiledCfg) and stores it.
-// Returns true if some stored depth is not positive (h <= 0 or NaN).
-template <typename T, int NWARP, int RY, bool XEDGE>
-__device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T *sV, T *__restrict__ oH,
-                                              T *__restrict__ oU, T *__restrict__ oV, int nx, int ny,
-                                              long long pitch, int x0, int y0, const Coef<T> &k)
+// The arithmetic of one thread's VX-cell column vector over tile-local rows
+// [r_begin, r_end): marching down, each y-face flux is computed once and
+// carried to the next row; x-faces come from the thread's cells and the two
+// neighbours in the same row.  The box holds the tile-local cell (c, r) at
+// shared index (r + row_off) * BW + c + AX.  Reflective walls are applied
+// where neighbours are formed (XEDGE: the tile touches an x-wall).  Rows
+// must lie inside the grid (0 <= y0 + r < ny).  ``store(r, h, hu, hv)``
+// receives each finished row.
+template <typename T, int VX, bool XEDGE, typename Store>
+__device__ __forceinline__ void strip_compute(const T *sH, const T *sU, const T *sV, int BW, int AX, int row_off,
+                                              int r_begin, int r_end, int cx, int gx, int nx, int ny, int y0,
+                                              const Coef<T> &k, Store &&store)
 {
-    bool bad = false;
-    using C = TiledCfg<T, NWARP, RY>;
-    constexpr int VX = C::VX;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int cx = lane * VX;  // tile-local first column of this thread
-    const int gx = x0 + cx;
-    const int rb = warp * RY;  // tile-local first row of this warp
-    if (y0 + rb >= ny) return false;
-    // shared-memory index of tile-local cell (c, r); the box starts at (-AX, -1)
-    auto sidx = [](int c, int r) { return (r + 1) * C::BW + c + C::AX; };
+    if (r_begin >= r_end) return;
+    auto sidx = [&](int c, int r) { return (r + row_off) * BW + c + AX; };
     const int pw = nx - gx;  // window position of the right wall ghost, if in 1..VX
 
     CellQ<T> cur[VX], nxt[VX];
     Flux3<T> gd[VX], gu[VX];
 
-    load_row<T, VX>(sH, sU, sV, sidx(cx, rb), k.hg, cur);
-    if (y0 + rb == 0) {
+    load_row<T, VX>(sH, sU, sV, sidx(cx, r_begin), k.hg, cur);
+    if (y0 + r_begin == 0) {
 #pragma unroll
         for (int p = 0; p < VX; ++p) nxt[p] = mirror_y(cur[p]);
     } else {
-        load_row<T, VX>(sH, sU, sV, sidx(cx, rb - 1), k.hg, nxt);
+        load_row<T, VX>(sH, sU, sV, sidx(cx, r_begin - 1), k.hg, nxt);
     }
 #pragma unroll
     for (int p = 0; p < VX; ++p) gd[p] = yface_flux(nxt[p], cur[p], k);
 
-#pragma unroll
-    for (int q = 0; q < RY; ++q) {
-        const int r = rb + q;
+#pragma unroll 1
+    for (int r = r_begin; r < r_end; ++r) {
         const int gy = y0 + r;
-        if (gy >= ny) break;
         if (gy + 1 == ny) {
 #pragma unroll
             for (int p = 0; p < VX; ++p) nxt[p] = mirror_y(cur[p]);
@@ -129,23 +124,67 @@ __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T 
             ov[p] = cur[p].v;
             lw_update(oh[p], ou[p], ov[p], F[p], F[p + 1], gd[p], gu[p], k);
         }
-        if (gx < nx) {
-#pragma unroll
-            for (int p = 0; p < VX; ++p) bad |= (gx + p < nx) && !(oh[p] > T(0));
-            // whole 16-byte vectors: columns past nx land in the row padding
-            const size_t o = (size_t)gy * (size_t)pitch + (size_t)gx;
-            store_vec<T, VX>(oH + o, oh);
-            store_vec<T, VX>(oU + o, ou);
-            store_vec<T, VX>(oV + o, ov);
-        }
+        store(r, oh, ou, ov);
 #pragma unroll
         for (int p = 0; p < VX; ++p) {
             cur[p] = nxt[p];
             gd[p] = gu[p];
         }
     }
-    return bad;
 }
 
+// One cell of a box, computed on its own from the 5-point neighbourhood (the
+// same face and update functions as strip_compute, so the same bits).
+template <typename T>
+__device__ __forceinline__ void box_cell(const T *sH, const T *sU, const T *sV, int BW, int AX, int row_off, int c,
+                                         int r, int gx, int gy, int nx, int ny, const Coef<T> &k, T &h, T &hu, T &hv)
+{
+    auto cell = [&](int cc, int rr) {
+        const int i = (rr + row_off) * BW + cc + AX;
+        return make_cell<T>(sH[i], sU[i], sV[i], k.hg);
+    };
+    const CellQ<T> C = cell(c, r);
+    const CellQ<T> L = gx == 0 ? mirror_x(C) : cell(c - 1, r);
+    const CellQ<T> R = gx == nx - 1 ? mirror_x(C) : cell(c + 1, r);
+    const CellQ<T> D = gy == 0 ? mirror_y(C) : cell(c, r - 1);
+    const CellQ<T> U = gy == ny - 1 ? mirror_y(C) : cell(c, r + 1);
+    const Flux3<T> Fl = xface_flux(L, C, k), Fr = xface_flux(C, R, k);
+    const Flux3<T> Gd = yface_flux(D, C, k), Gu = yface_flux(C, U, k);
+    h = C.h;
+    hu = C.u;
+    hv = C.v;
+    lw_update(h, hu, hv, Fl, Fr, Gd, Gu, k);
+}
+
+// Computes one output tile from the staged box (see TiledCfg) and stores it.
+// Returns true if some stored depth is not positive (h <= 0 or NaN).
+template <typename T, int NWARP, int RY, bool XEDGE>
+__device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T *sV, T *__restrict__ oH,
+                                              T *__restrict__ oU, T *__restrict__ oV, int nx, int ny,
+                                              long long pitch, int x0, int y0, const Coef<T> &k)
+{
+    using C = TiledCfg<T, NWARP, RY>;
+    constexpr int VX = C::VX;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int cx = lane * VX;
+    const int gx = x0 + cx;
+    const int rb = warp * RY;
+    const int re = min(rb + RY, ny - y0);
+    bool bad = false;
+    strip_compute<T, VX, XEDGE>(sH, sU, sV, C::BW, C::AX, 1, rb, re, cx, gx, nx, ny, y0, k,
+                                [&](int r, const T(&oh)[VX], const T(&ou)[VX], const T(&ov)[VX]) {
+                                    if (gx < nx) {
+#pragma unroll
+                                        for (int p = 0; p < VX; ++p) bad |= (gx + p < nx) && !(oh[p] > T(0));
+                                        // whole 16-byte vectors: columns past nx land in the row padding
+                                        const size_t o = (size_t)(y0 + r) * (size_t)pitch + (size_t)gx;
+                                        store_vec<T, VX>(oH + o, oh);
+                                        store_vec<T, VX>(oU + o, ou);
+                                        store_vec<T, VX>(oV + o, ov);
+                                    }
+                                });
+    return bad;
+}
 
 }  // namespace swe

@@ -26,7 +26,7 @@ SWE_FLAG_NONPOSITIVE, SWE_FLAG_MASS, SWE_FLAG_TIMEOUT, SWE_FLAG_FALLBACK = 1, 2,
  SWE_BQ_STAGES, SWE_BQ_DEPTH, SWE_BQ_GRAPH, SWE_BQ_LAUNCHES, SWE_BQ_TUNED, SWE_BQ_CELLS,
  SWE_BQ_VARIANT_COUNT) = range(13)
 (SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
- SWE_Q_STATE_PTR) = range(7)
+ SWE_Q_STATE_PTR, SWE_Q_STEPS_PER_LAUNCH) = range(8)
 
 
 class SweError(RuntimeError):
@@ -84,10 +84,12 @@ _SIGS = {
     "swe_net_prep_input": (_i, [_vp, _i, _vp, _vp, _ll, _ll, _ll, _vp]),
     "swe_net_infer": (_i, [_vp, _i, _vp, _vp]),
     "swe_net_apply": (_i, [_vp, _i, _vp, _ll, _ll, _ll, _i, _vp]),
+    "swe_net_correct": (_i, [_vp, _i, _vp, _ll, _ll, _ll, _i, _vp]),
     "swe_net_make_target": (_i, [_vp, _i, _vp, _vp, _ll, _ll, _ll, ctypes.c_float, _vp, _vp]),
     "swe_net_train_step": (_i, [_vp, _i, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i,
                                 ctypes.POINTER(_d), _vp, _vp, _vp]),
     "swe_net_check": (_i, [_vp, _vp]),
+    "swe_selftest_gelu": (_i, [_vp, _vp, _i, _i, _vp]),
     "swe_downsample": (_i, [_i, _vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
 
@@ -225,11 +227,12 @@ def _buf(a, dtype_np):
 class Grid:
     """One nx x ny grid on the current CUDA device (owns a swe_ctx)."""
 
-    def __init__(self, nx, ny, dx, dy, dt, g, dtype="f32", kernel=SWE_KERNEL_AUTO, depth=0):
+    def __init__(self, nx, ny, dx, dy, dt, g, dtype="f32", kernel=SWE_KERNEL_AUTO, depth=0, variant=None):
         o = swe_options_init()
         o.dtype = SWE_F64 if dtype in ("f64", np.float64) else SWE_F32
         o.kernel = kernel
         o.depth = depth
+        o.reserved[0] = 0 if variant is None else int(variant) + 1
         self.np_dtype = np.float64 if o.dtype == SWE_F64 else np.float32
         self.nx, self.ny = nx, ny
         self.ctx = swe_create_ex(nx, ny, dx, dy, dt, g, o)
@@ -472,6 +475,10 @@ class Net:
     def apply(self, n, state_ptr, img_stride, plane_stride, pitch, project_mass=True, stream=None):
         check(lib().swe_net_apply(self.t, n, state_ptr, img_stride, plane_stride, pitch, int(project_mass),
                                   stream if stream is not None else current_stream()), "swe_net_apply")
+
+    def correct(self, n, state_ptr, img_stride, plane_stride, pitch, project_mass=True, stream=None):
+        check(lib().swe_net_correct(self.t, n, state_ptr, img_stride, plane_stride, pitch, int(project_mass),
+                                    stream if stream is not None else current_stream()), "swe_net_correct")
 
     def make_target(self, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, target_ptr, clip=0.0, stream=None):
         check(lib().swe_net_make_target(self.t, n, next_ptr, lw_ptr, img_stride, plane_stride, pitch, clip,

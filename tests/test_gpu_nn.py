@@ -139,3 +139,28 @@ def test_training_reduces_the_loss_on_a_fixed_batch():
         for _ in range(300):
             last, _ = net.train_step(n, tdev.data_ptr(), lr=3e-3)
     assert last < first / 5, (first, last)
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_device_erf_and_gelu_within_published_bound(which):
+    """The network's erf (Abramowitz & Stegun 7.1.26, |error| <= 1.5e-7) and
+    the GELU / GELU' built on it, against scipy's erf in FP64."""
+    import torch
+    from scipy.special import erf
+    from paper_1107_2157_gb300 import swe
+    z = np.concatenate([np.linspace(-8, 8, 20001), [0.0, 1e-8, -1e-8, 30.0, -30.0]]).astype(np.float32)
+    zd = torch.from_numpy(z).cuda()
+    out = torch.zeros_like(zd)
+    swe.check(swe.lib().swe_selftest_gelu(zd.data_ptr(), out.data_ptr(), z.size, which, None), "gelu")
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    x = z.astype(np.float64)
+    if which == 0:
+        ref, tol = erf(x), 1.5e-7 + 4e-7  # published bound + FP32 evaluation
+        assert np.abs(got - ref).max() <= tol
+    elif which == 1:
+        ref = nn.gelu(x)
+        assert np.abs(got - ref).max() <= 1e-6 * np.maximum(1.0, np.abs(x)).max()
+    else:
+        ref = nn.gelu_grad(x)
+        assert np.abs(got - ref).max() <= 2e-6
