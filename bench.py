@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--eval-trajectories", type=int, default=200)
     p.add_argument("--serve-instances", type=int, default=1024)
     p.add_argument("--passes", type=int, default=1)
+    p.add_argument("--ensemble-count", type=int, default=512)
+    p.add_argument("--no-tune", action="store_true", help="ensemble: default kernel variant, no autotuning")
+    p.add_argument("--skip-train", action="store_true",
+                   help="learned: serve with untrained weights (kernel timing and profiling only)")
     p.add_argument("--tune-cache", default=None)
     return p.parse_args()
 
@@ -400,7 +404,7 @@ def run_ensemble(args):
     from paper_1107_2157_gb300 import Batch, swe
 
     torch.cuda.set_device(0)
-    sizes = si.ensemble_sizes(seed=2, count=512)
+    sizes = si.ensemble_sizes(seed=2, count=args.ensemble_count)
     t0 = time.perf_counter()
     states = [si.ensemble_state(2, i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
     t_ic = time.perf_counter() - t0
@@ -415,7 +419,8 @@ def run_ensemble(args):
         dts = b.cfl_dt(CFL, stream=sp)
         b.set_dt(dts, stream=sp)
         t0 = time.perf_counter()
-        b.tune(args.tune_cache, stream=sp)
+        if not args.no_tune:
+            b.tune(args.tune_cache, stream=sp)
         t_tune = time.perf_counter() - t0
         b.step(args.warmup, stream=sp)
         torch.cuda.synchronize()
@@ -469,6 +474,17 @@ def run_learned(args):
     sp = torch.cuda.current_stream().cuda_stream
     setup = C.Setup(n_fine=1024, factor=4, dt_fine=0.04, coarse_steps=64)
     nc = setup.n_coarse
+    if args.skip_train:
+        # kernel timing only: untrained weights, fixed scales, no error report
+        states = si.corrector_states(range(10000, 10000 + args.serve_instances), setup.n_fine, setup.dam_fraction)
+        params, norm = C.init_params(0), [0.0, 5e-4, 1.4e-3, 1.2e-5, 3e-5]
+        for _ in range(2):
+            out = C.serve(setup, states, params, norm, fallback=False)
+            out["coarse"].close()
+        print(json.dumps({"workload": "learned-serving-kernels", "instances": args.serve_instances,
+                          "coarse_steps": setup.coarse_steps, "seconds": out["seconds"],
+                          "ms_per_coarse_step": 1e3 * out["seconds"] / setup.coarse_steps}), flush=True)
+        return
     t0 = time.perf_counter()
     res = C.train(setup, range(0, args.train_trajectories), B=32, lr=1e-3, passes=args.passes, gen_batch=64)
     t_train = time.perf_counter() - t0

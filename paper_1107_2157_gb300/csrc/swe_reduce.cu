@@ -136,9 +136,11 @@ __global__ void __launch_bounds__(1024) sum_final_kernel(RedGrid one, const RedG
 // ---------------------------------------------------------------------------
 constexpr float kCflSlack = 1.0f / 65536.0f;
 
-__device__ __forceinline__ bool cell_bad(double h, double u, double v)
+// Depth not positive, or a value not finite (checked in the data's own type).
+template <typename T>
+__device__ __forceinline__ bool cell_bad(T h, T u, T v)
 {
-    return !(h > 0.0) || !isfinite(h) || !isfinite(u) || !isfinite(v);
+    return !(h > T(0)) || !isfinite(h) || !isfinite(u) || !isfinite(v);
 }
 
 template <typename T, bool MANY>
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(RedGrid one, con
         const size_t ro = (size_t)j * (size_t)G.pitch;
         for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
             const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
-            if (cell_bad((double)h, (double)u, (double)v)) {
+            if (cell_bad<T>(h, u, v)) {
                 bad += 1.0;
                 continue;
             }
@@ -214,7 +216,9 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, con
     const size_t n = gridDim.y;
     const size_t P = (size_t)gridDim.x * n;
     const double *th = scratch + 3 * P + 3 * (size_t)blockIdx.y;
-    const double thx = th[0], thy = th[1];
+    // thresholds as floats rounded toward -inf: the screen keeps every
+    // candidate the FP64 threshold keeps, and compares in FP32
+    const float thx = __double2float_rd(th[0]), thy = __double2float_rd(th[1]);
     double sx = 0.0, sy = 0.0;
     T lhx = T(-1), lux = T(0), lhy = T(-1), lvy = T(0);  // last exactly evaluated inputs
     double lsx = 0.0, lsy = 0.0;
@@ -222,12 +226,12 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, con
         const size_t ro = (size_t)j * (size_t)G.pitch;
         for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
             const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
-            if (cell_bad((double)h, (double)u, (double)v)) continue;
+            if (cell_bad<T>(h, u, v)) continue;
             const float hf = (float)h;
             const float inv = rcp(hf);
             const float c = sqrtf(g32 * hf);
-            const double ex = (double)(c + fabsf((float)u * inv));
-            const double ey = (double)(c + fabsf((float)v * inv));
+            const float ex = c + fabsf((float)u * inv);
+            const float ey = c + fabsf((float)v * inv);
             if (ex >= thx) {
                 if (!(h == lhx && u == lux)) {
                     lhx = h;
