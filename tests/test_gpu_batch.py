@@ -46,7 +46,7 @@ def test_batch_matches_oracle_per_instance():
         for i, s in enumerate(states):
             got = b.get_state(i)
             ref = oracle.run(s.h, s.hu, s.hv, dxs[i], dys[i], dts[i], G, steps)
-            errs = rel_errors(got, ref, floor_frac=1e-2)
+            errs = rel_errors(got, ref)
             assert max(errs) <= TOL_F32, (i, SIZES[i], errs)
 
 

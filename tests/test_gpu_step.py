@@ -59,7 +59,7 @@ def test_ragged_sizes_with_flow_at_walls(kernel, dtype, nx, ny):
     dt = oracle.cfl_dt(s.h, s.hu, s.hv, dx, dy, G, 0.3)
     ref = _oracle(s, dx, dy, dt, 20)
     got = run_gpu(s, dx, dy, dt, G, 20, dtype, KERNELS[kernel])
-    errs = rel_errors(got, ref, floor_frac=1e-2)
+    errs = rel_errors(got, ref)
     assert max(errs) <= (TOL_F64 if dtype == "f64" else TOL_F32), errs
 
 
@@ -156,7 +156,15 @@ def _full_windows(n, w=8, seed=12):
         inner.append((i0, i0 + w - 1, j0, j0 + w - 1))
     # tile seams of the 128x32 (FP32) and 64x32 (FP64) tiles
     seams = [(128 * 20 - 3, 128 * 20 + 4, 32 * 50 - 3, 32 * 50 + 4)]
-    return corners + edges + inner + seams
+    # on the slopes of the first bumps of the initial state, where the flow
+    # after 100 steps is far from still water
+    slopes = []
+    for b in si.large_grid_bumps(1, n)[:6]:
+        for (ox, oy) in ((b.sigma, 0.0), (0.0, -0.5 * b.sigma)):
+            i0 = int(min(max(round(b.cx + ox) - w // 2, 1), n - w + 1))
+            j0 = int(min(max(round(b.cy + oy) - w // 2, 1), n - w + 1))
+            slopes.append((i0, i0 + w - 1, j0, j0 + w - 1))
+    return corners + edges + inner + seams + slopes
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -189,7 +197,7 @@ def test_full_size_8192_sampled_windows(dtype):
 
     tol = TOL_F64 if dtype == "f64" else TOL_F32
     scale_h = float(h0.max())
-    floor = 1e-3 * scale_h * math.sqrt(G * scale_h)
+    floor = scale_h * math.sqrt(G * scale_h)
     for w in _full_windows(n):
         ref = oracle.run_window(ic, n, n, w, 1.0, 1.0, dt, G, steps)
         i0, i1, j0, j1 = w
@@ -284,8 +292,8 @@ def test_two_step_kernel_full_size_windows_against_oracle():
         return h, np.zeros_like(h), np.zeros_like(h)
 
     scale_h = float(h0.max())
-    floor = 1e-3 * scale_h * math.sqrt(G * scale_h)
-    for w in _full_windows(n)[:6]:
+    floor = scale_h * math.sqrt(G * scale_h)
+    for w in _full_windows(n)[-8:]:
         ref = oracle.run_window(ic, n, n, w, 1.0, 1.0, dt, G, steps)
         i0, i1, j0, j1 = w
         for k in range(3):
