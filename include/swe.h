@@ -344,8 +344,27 @@ swe_status swe_net_train_step(swe_net *net, int n, const float *target, float lr
                               double *loss_out, float *grads_out, float *resid_out, void *stream);
 /* Synchronises and returns the device error word of the net's kernels. */
 swe_status swe_net_check(swe_net *net, void *stream);
+/* The learned coarse step of every instance of batch b, n_steps times, in
+ * ONE persistent launch (stream-ordered): each step is the coarse
+ * Lax-Wendroff step (Sec. 3), the network on its normalised FP32 increment
+ * (as swe_net_prep_input with base = the state the step started from) and
+ * the scaled residual added to the Lax-Wendroff result; with project_mass
+ * the per-image mean of the h correction is removed (the step keeps the
+ * Lax-Wendroff mass up to rounding).  Same arithmetic as swe_batch_step(1)
+ * + swe_net_prep_input + swe_net_correct per step, but the activations
+ * never leave the SM: one CTA sweeps one instance at a time, row by row.
+ * Uses the net's current weights and normalisation; the net's image size is
+ * not used.  Every instance must be at most 256 cells wide
+ * (SWE_EUNSUPPORTED otherwise); instances may differ in size.  A step that
+ * produces h <= 0 (or NaN) sets SWE_FLAG_NONPOSITIVE for the instance
+ * (swe_batch_status); a device-side wait that gives up records
+ * SWE_ETIMEOUT there too.  The batch's current buffer advances as with
+ * swe_batch_step. */
+swe_status swe_batch_learned_step(swe_batch *b, swe_net *net, int n_steps, int project_mass, void *stream);
 /* Self-test of the network's activation on the device: out[i] = erf(z[i])
- * (which = 0), gelu(z[i]) (1) or gelu'(z[i]) (2); device pointers. */
+ * (which = 0; Abramowitz & Stegun 7.1.26, |error| <= 1.5e-7), gelu(z[i])
+ * (1; the forward activation, erf from A&S 7.1.27, |error| <= 6.9e-4) or
+ * gelu'(z[i]) (2; with 7.1.26); device pointers. */
 swe_status swe_selftest_gelu(const float *z, float *out, int n, int which, void *stream);
 /* factor x factor block average (factor 1..4) of n images (3 planes each)
  * of (factor Hc) x (factor Wc) fine cells into Hc x Wc coarse cells; strides

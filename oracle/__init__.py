@@ -5,8 +5,9 @@ Plain, slow, FP64 code that states what the GPU path must compute:
     update of the two-step Lax-Wendroff scheme (Sec. 3, step equations;
     Sec. 3.1, Fortran statements) -- in ``swe_oracle.c``;
   * the FP64 mass and CFL time step (Sec. 3) -- in ``swe_oracle.c``;
-  * the 4x4 block-average restriction and the corrector network -- in
-    ``downsample.py`` and ``nn.py`` (numpy, FP64).
+  * the block-average restriction and the corrector network -- in
+    ``nn.py`` (numpy, FP64); the learned coarse step built from them and
+    the Lax-Wendroff step -- in ``learned.py``.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA

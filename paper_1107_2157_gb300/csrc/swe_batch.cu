@@ -30,20 +30,13 @@
 #include <vector>
 
 #include "swe_tile.cuh"
+#include "swe_views.cuh"
 
 namespace swe {
 
 struct TileRec {
     int inst;
     unsigned short bx, by;  // tile column / row within the instance
-};
-
-struct BatchInst {
-    float *buf[2];       // three planes (H, U, V) per buffer
-    long long plane;     // elements per plane
-    long long pitch;     // elements per row
-    int nx, ny;
-    Coef<float> k;
 };
 
 // ---------------------------------------------------------------------------
@@ -223,6 +216,29 @@ struct swe_batch {
     long long launches = 0;
     int tuned = 0;
 };
+
+namespace swe {
+
+bool batch_view(swe_batch *b, BatchView *v)
+{
+    if (!b || !v) return false;
+    v->n = b->n;
+    v->cur = b->cur;
+    v->sms = b->sms;
+    v->d_inst = b->d_inst;
+    v->h_inst = b->h_inst.data();
+    v->d_flags = b->d_flags;
+    v->d_err = b->d_err;
+    return true;
+}
+
+void batch_advance(swe_batch *b, int n_steps)
+{
+    b->cur ^= (n_steps & 1);
+    b->launches += 1;
+}
+
+}  // namespace swe
 
 static swe_status st_of(cudaError_t e)
 {

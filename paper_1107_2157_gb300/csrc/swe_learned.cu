@@ -1,0 +1,596 @@
+// swe_learned.cu -- the learned coarse step fused into one persistent
+// launch: for every instance of a batch and every step, the coarse
+// Lax-Wendroff step (Sec. 3), the corrector network (zero-padded 3x3
+// convolutions 3 -> 32 -> 32 -> 3 with GELU, BF16 operands, FP32
+// accumulation in tensor memory) on the normalised increment, and the
+// corrected update with the mass projection, all on one SM per instance.
+// The network has no counterpart in the paper.
+//
+// A CTA owns whole instances (up to 256 cells wide) and sweeps each one row
+// by row.  Tick t of a sweep computes, in a software pipeline two rows deep
+// per stage:
+//   LW  row t      CUDA cores; the network input x0[t] (the normalised
+//                  increment, 16 bf16 channels) goes to a 2-row ring
+//   E1  row t-2    GELU of layer 1's accumulator -> a1 ring (2 rows)
+//   E2  row t-4    GELU of layer 2's accumulator -> a2 ring (2 rows)
+//   E3  row t-6    layer 3's output, scaled, added to the LW row -> HBM
+// The MMAs run by input row: input row j of a layer feeds output rows j+1,
+// j, j-1 through kernel rows ky = 0, 1, 2, so one MMA per (kx, K step, half
+// row) with N = 3 x (output channels) -- the B operand is the three ky
+// weight blocks side by side -- adds row j's contributions to the three
+// output rows' accumulators at once.  Each layer keeps its accumulators in
+// a ring of three TMEM blocks (output row r in block r mod 3); the weights
+// are stored in three rotations so that block b of the MMA's output always
+// meets the ky that row r = b (mod 3) needs.  An accumulator starts from
+// the bias (the epilogue that reads output row r re-arms the block for row
+// r+3), so every MMA accumulates.  Per tick a separate warp -- one elected
+// lane -- issues layer 1 on x0[t] once E1 has re-armed its block, layer 2
+// on a1[t-2] after E2, and layer 3 on a2[t-4] after E3; their results are
+// read one tick later, so the tensor core runs under the next tick's CUDA
+// work.  The A operand is a ring row at a shifted shared-memory address
+// (kx): no im2col copy exists.  Pixels outside the grid are zero in the
+// rings and rows outside it are never MMA inputs: the zero padding.
+//
+// Mass projection: the mean of the h correction over the instance is known
+// only when the sweep ends, so it is kept as a pending offset m: the state
+// written by a sweep is (true h) + m, the next sweep subtracts m as it
+// loads, and after the last step every h is corrected in place.  The
+// arithmetic is the same as the unfused path's (correct, then subtract the
+// mean).
+#include <algorithm>
+#include <mutex>
+
+#include "swe_gelu.cuh"
+#include "swe_tc.cuh"
+#include "swe_views.cuh"
+
+#ifndef SWE_LEARN_NG
+#define SWE_LEARN_NG 2
+#endif
+
+namespace swe {
+
+namespace {
+
+__host__ __device__ constexpr size_t lal16(size_t x) { return (x + 15) / 16 * 16; }
+
+template <int NH, int NG>
+struct LearnCfg {
+    static constexpr int PX = 128 * NH;      // pixels of a row (the MMA's M per half)
+    static constexpr int PXB = PX + 2;       // with a zero pixel at each end
+    static constexpr int STRIP = PXB * 16;   // one 8-channel strip of a ring row, bytes
+    static constexpr int X0_ROW = 2 * STRIP; // 16 channels
+    static constexpr int A_ROW = 4 * STRIP;  // 32 channels
+    static constexpr int RING = 2, LW_SLOTS = 7;
+    static constexpr int NCW = 4 * NH * NG;  // compute warps; one more issues the MMAs
+    static constexpr int THREADS = (NCW + 1) * 32;
+    static constexpr int CPT = 32 / NG;      // hidden channels per epilogue thread
+    // Weight images: per layer, rotation rho (0..2), kx, K step s, a 16 x 3C
+    // K-major B operand [K core 2][N core 3C/8][8 x 16 B].
+    static constexpr size_t IMG1 = 2 * 12 * 128, IMG2 = 2 * 12 * 128, IMG3 = 2 * 6 * 128;
+    static constexpr size_t W1_B = 9 * 1 * IMG1, W2_B = 9 * 2 * IMG2, W3_B = 9 * 2 * IMG3;
+    static constexpr size_t OFF_W1 = 0;
+    static constexpr size_t OFF_W2 = OFF_W1 + W1_B;
+    static constexpr size_t OFF_W3 = OFF_W2 + W2_B;
+    static constexpr size_t OFF_X0 = OFF_W3 + W3_B;
+    static constexpr size_t OFF_A1 = lal16(OFF_X0 + (size_t)RING * X0_ROW);
+    static constexpr size_t OFF_A2 = lal16(OFF_A1 + (size_t)RING * A_ROW);
+    static constexpr size_t OFF_LW = lal16(OFF_A2 + (size_t)RING * A_ROW);
+    static constexpr size_t OFF_XR = OFF_LW + (size_t)LW_SLOTS * 3 * PX * 4;
+    static constexpr size_t OFF_BIAS = OFF_XR + (size_t)2 * 3 * PXB * 4;
+    static constexpr size_t OFF_RED = lal16(OFF_BIAS + 80 * 4);
+    static constexpr size_t OFF_BAR = lal16(OFF_RED + 16 * 8);
+    static constexpr size_t SMEM = OFF_BAR + 128;
+    // TMEM per layer: per half-row of 128 pixels, three row blocks of C
+    // columns (C = 32, 32, 16).
+    static constexpr uint32_t ACC1 = 0, ACC2 = NH * 96, ACC3 = 2 * NH * 96;
+    static constexpr uint32_t TMEM_USED = ACC3 + NH * 48;
+    static constexpr uint32_t TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
+};
+
+struct LearnArgs {
+    const BatchInst *inst;
+    int n_inst;
+    int n_steps;
+    int parity0;
+    const bf16 *w1, *w2, *w3;  // B-operand images (global)
+    const float *bias;         // 80 floats
+    float inv_sh, inv_su;      // input normalisation of the increment
+    float os_h, os_u;          // output scales of the residual
+    int project;               // zero-mean h correction
+    int *flags;
+    int *err;
+};
+
+// mbarriers (shared memory, in this order).  Each advances one phase per
+// batch; no barrier runs two phases ahead of a waiter, because every
+// arrival for batch t+1 follows its warp's wait on batch t.
+enum { B_RDY1 = 0, B_RDY2 = 1, B_RDY3 = 2, B_L1 = 3, B_L2 = 4, B_L3 = 5, B_FIN = 6, B_COUNT = 7 };
+
+__device__ __forceinline__ void named_bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+
+// True on exactly one lane of the (converged) warp.
+__device__ __forceinline__ bool elect_one()
+{
+    uint32_t p;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "elect.sync _|P, 0xffffffff;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}"
+        : "=r"(p));
+    return p != 0;
+}
+
+// Two floats rounded to bf16 (nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// A warp hands its shared-memory writes (generic proxy) and its finished
+// TMEM reads over to the MMA warp: every lane fences, lane 0 arrives.
+__device__ __forceinline__ void publish(uint64_t *bar, int lane)
+{
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+}
+
+__device__ __forceinline__ int mod3(int r) { return r - 3 * (r / 3); }
+
+// Sixteen bias values (shared memory, 16-byte aligned) into registers.
+__device__ __forceinline__ void load16(const float *p, float (&b)[16])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 f = *reinterpret_cast<const float4 *>(p + 4 * k);
+        b[4 * k] = f.x;
+        b[4 * k + 1] = f.y;
+        b[4 * k + 2] = f.z;
+        b[4 * k + 3] = f.w;
+    }
+}
+
+// Arms CPT accumulator columns at taddr with the bias (TMEM store).
+template <int CPT>
+__device__ __forceinline__ void arm(uint32_t taddr, const float *bias)
+{
+#pragma unroll
+    for (int c = 0; c < CPT / 16; ++c) {
+        float b[16];
+        load16(bias + 16 * c, b);
+        tc::st_x16(taddr + 16 * c, b);
+    }
+}
+
+// Hidden-layer epilogue of one pixel: CPT finished accumulator columns at
+// taddr (bias included) -> GELU -> bf16 -> CPT/8 strips of a ring row at
+// dst (strip stride ``strip``), zeros where the pixel is outside the grid;
+// then the columns are re-armed with the bias.
+template <int CPT>
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bias, unsigned char *dst, int strip,
+                                                bool valid)
+{
+    float v[CPT];
+    if constexpr (CPT == 32)
+        tc::ld_x32(taddr, v);
+    else
+        tc::ld_x16(taddr, v);
+    arm<CPT>(taddr, bias);
+#pragma unroll
+    for (int c = 0; c < CPT / 8; ++c) {
+        const float y0 = gelu_f(v[8 * c + 0]), y1 = gelu_f(v[8 * c + 1]);
+        const float y2 = gelu_f(v[8 * c + 2]), y3 = gelu_f(v[8 * c + 3]);
+        const float y4 = gelu_f(v[8 * c + 4]), y5 = gelu_f(v[8 * c + 5]);
+        const float y6 = gelu_f(v[8 * c + 6]), y7 = gelu_f(v[8 * c + 7]);
+        const uint4 o = make_uint4(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3), pack_bf16x2(y4, y5), pack_bf16x2(y6, y7));
+        *reinterpret_cast<uint4 *>(dst + c * strip) = valid ? o : zero4();
+    }
+}
+
+// Copies the per-tap B images of one layer (global; block (tap, s) is
+// [K core 2][N core NC][8 x 16 B]) into the rotated, concatenated images
+// (shared): image (rho, kx, s) has N block b = the weights of tap
+// (ky, kx) with ky = (rho - b + 1) mod 3, for an input row j = rho (mod 3)
+// whose MMA output block b holds output row r = b (mod 3), ky = j - r + 1.
+__device__ __forceinline__ void rotate_weights(const bf16 *src, unsigned char *dst, int NC, int NKS, int tid,
+                                               int nthreads)
+{
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const int cores_img = 2 * 3 * NC;
+    const int total = 9 * NKS * cores_img * 8;
+    for (int e = tid; e < total; e += nthreads) {
+        const int u = e & 7, core = e >> 3;
+        const int nip = core % (3 * NC), ki = (core / (3 * NC)) & 1, img = core / cores_img;
+        const int sk = img % NKS, kx = (img / NKS) % 3, rho = img / (3 * NKS);
+        const int b = nip / NC, ni = nip % NC;
+        const int ky = (rho + 4 - b) % 3, tap = 3 * ky + kx;
+        d[e] = __ldg(s + ((size_t)((tap * NKS + sk) * 2 * NC + ki * NC + ni) * 8 + u));
+    }
+}
+
+template <int NH, int NG>
+__global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_kernel(const LearnArgs a)
+{
+    using C = LearnCfg<NH, NG>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sW1 = smem + C::OFF_W1;
+    unsigned char *sW2 = smem + C::OFF_W2;
+    unsigned char *sW3 = smem + C::OFF_W3;
+    unsigned char *sX0 = smem + C::OFF_X0;
+    unsigned char *sA1 = smem + C::OFF_A1;
+    unsigned char *sA2 = smem + C::OFF_A2;
+    float *sLW = reinterpret_cast<float *>(smem + C::OFF_LW);
+    float *sXR = reinterpret_cast<float *>(smem + C::OFF_XR);
+    float *sBias = reinterpret_cast<float *>(smem + C::OFF_BIAS);
+    double *sRed = reinterpret_cast<double *>(smem + C::OFF_RED);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + B_COUNT);
+    volatile int *sAbort = reinterpret_cast<volatile int *>(bars + B_COUNT) + 1;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(bars + B_RDY1, C::NCW);
+        mbar_init(bars + B_RDY2, C::NCW);
+        mbar_init(bars + B_RDY3, C::NCW);
+        mbar_init(bars + B_L1, 1);
+        mbar_init(bars + B_L2, 1);
+        mbar_init(bars + B_L3, 1);
+        mbar_init(bars + B_FIN, 1);
+        fence_mbar_init();
+        *sAbort = 0;
+    }
+    // weights (rotated, concatenated), bias, and zeroed rings
+    rotate_weights(a.w1, sW1, 4, 1, tid, C::THREADS);
+    rotate_weights(a.w2, sW2, 4, 2, tid, C::THREADS);
+    rotate_weights(a.w3, sW3, 2, 2, tid, C::THREADS);
+    for (int i = tid; i < 80; i += C::THREADS) sBias[i] = a.bias[i];
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(sX0);
+        const int nz = (int)((C::OFF_LW - C::OFF_X0) / 16);
+        for (int i = tid; i < nz; i += C::THREADS) z[i] = zero4();
+    }
+    fence_proxy_async_smem();
+    if (warp == C::NCW) tc::tmem_alloc(tslot, C::TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    if (warp == C::NCW) {
+        // ------------------------------------------------------------------
+        // MMA issue.  Batch t of a sweep: layer 1 on input row t, layer 2 on
+        // row t-2, layer 3 on row t-4 (rows outside the grid skipped).  The
+        // whole warp runs the loop so that the operands stay warp-uniform;
+        // one elected lane issues.
+        // ------------------------------------------------------------------
+        constexpr uint32_t id96 = tc::idesc_bf16(128, 96), id64 = tc::idesc_bf16(128, 64);
+        constexpr uint32_t id48 = tc::idesc_bf16(128, 48), id32 = tc::idesc_bf16(128, 32);
+        // Descriptors of the first byte of each operand region; an operand
+        // at byte offset o has descriptor base + (o >> 4) (the address field
+        // holds addr >> 4 and shared memory is < 256 KB, so the sum never
+        // carries out of it).
+        const uint64_t dX0 = tc::smem_desc(sX0, C::STRIP, 128), dA1 = tc::smem_desc(sA1, C::STRIP, 128),
+                       dA2 = tc::smem_desc(sA2, C::STRIP, 128);
+        const uint64_t dW1 = tc::smem_desc(sW1, 12 * 128, 128), dW2 = tc::smem_desc(sW2, 12 * 128, 128),
+                       dW3 = tc::smem_desc(sW3, 6 * 128, 128);
+        // All MMAs of input row j of one layer: kx, K steps, half rows.  Row
+        // 0 has no output row -1 (whose block is row 2's): N covers blocks
+        // 0 and 1 only.
+        auto layer = [&](uint64_t dA, int row_bytes, int j, int nks, uint64_t dW, int img, uint32_t acc, int ncol3,
+                         uint32_t idesc_full, uint32_t idesc_first) {
+            const uint32_t idesc = j == 0 ? idesc_first : idesc_full;
+            const int rho = mod3(j);
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                for (int sk = 0; sk < 2; ++sk) {
+                    if (sk >= nks) break;
+                    const uint32_t ao = (uint32_t)((j & 1) * row_bytes) + (uint32_t)(2 * sk * C::STRIP) +
+                                        (uint32_t)(kx * 16);
+                    const uint32_t bo = (uint32_t)(((rho * 3 + kx) * nks + sk) * img);
+#pragma unroll
+                    for (int hh = 0; hh < NH; ++hh)
+                        tc::mma_bf16(acc + (uint32_t)(hh * ncol3), dA + ((ao + (uint32_t)(2048 * hh)) >> 4),
+                                     dW + (bo >> 4), idesc, true);
+                }
+        };
+        // Waits (whole warp) for phase ``par`` of ``bar``; false once anything
+        // has given up.
+        auto wait_all = [&](uint64_t *bar, uint32_t par) {
+            bool go = !*sAbort && mbar_wait_bounded(bar, par, a.err);
+            go = __all_sync(0xffffffffu, go);
+            if (!go && lane == 0) *sAbort = 1;
+            tc::fence_after_sync();
+            return go;
+        };
+        uint32_t nb = 0;
+        for (int i = blockIdx.x; i < a.n_inst; i += gridDim.x) {
+            const int H = a.inst[i].ny;
+            const int T = H + 6;
+            for (int k = 0; k < a.n_steps; ++k) {
+                for (int t = 0; t + 1 < T; ++t, ++nb) {
+                    const uint32_t par = nb & 1u;
+                    if (!wait_all(bars + B_RDY1, par)) continue;
+                    if (elect_one()) {
+                        if (t < H) layer(dX0, C::X0_ROW, t, 1, dW1, (int)C::IMG1, tmem + C::ACC1, 96, id96, id64);
+                        tc::commit(bars + B_L1);
+                    }
+                    __syncwarp();
+                    if (!wait_all(bars + B_RDY2, par)) continue;
+                    if (elect_one()) {
+                        if (t - 2 >= 0 && t - 2 < H)
+                            layer(dA1, C::A_ROW, t - 2, 2, dW2, (int)C::IMG2, tmem + C::ACC2, 96, id96, id64);
+                        tc::commit(bars + B_L2);
+                    }
+                    __syncwarp();
+                    if (!wait_all(bars + B_RDY3, par)) continue;
+                    if (elect_one()) {
+                        if (t - 4 >= 0 && t - 4 < H)
+                            layer(dA2, C::A_ROW, t - 4, 2, dW3, (int)C::IMG3, tmem + C::ACC3, 48, id48, id32);
+                        tc::commit(bars + B_L3);
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        // every MMA issued has completed before the accumulators are freed
+        if (elect_one()) tc::commit(bars + B_FIN);
+        __syncwarp();
+        mbar_wait_bounded(bars + B_FIN, 0, a.err);
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------
+        // Compute warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31: pixel
+        // px = 128 hh + 32 q + lane of half hh, channel group g.  Group 0
+        // (PX threads, one per pixel) also runs the Lax-Wendroff step and
+        // the output stage.
+        // ------------------------------------------------------------------
+        const int q = warp & 3, hh = (warp >> 2) % NH, g = warp / (4 * NH);
+        const int px = 128 * hh + 32 * q + lane;
+        const bool lw_thread = g == 0;
+        const uint32_t tl = (uint32_t)(32 * q) << 16;
+        // this thread's accumulator columns (block 0) of each layer
+        const uint32_t t1 = tmem + tl + C::ACC1 + hh * 96 + C::CPT * g;
+        const uint32_t t2 = tmem + tl + C::ACC2 + hh * 96 + C::CPT * g;
+        const uint32_t t3 = tmem + tl + C::ACC3 + hh * 48;
+        const int sw = (C::CPT / 8) * g * C::STRIP + (px + 1) * 16;  // ring offset of this thread's strips
+        uint32_t nb = 0;  // batches of the finished sweeps
+        // waits for ``bar`` (per thread); records a give-up for everyone
+        auto wait = [&](uint64_t *bar, uint32_t par) {
+            if (!*sAbort && !mbar_wait_bounded(bar, par, a.err)) *sAbort = 1;
+            __syncwarp();
+            tc::fence_after_sync();
+        };
+        for (int i = blockIdx.x; i < a.n_inst; i += gridDim.x) {
+            const BatchInst I = a.inst[i];
+            const int W = I.nx, H = I.ny, T = H + 6;
+            const long long pitch = I.pitch, plane = I.plane;
+            const Coef<float> kc = I.k;
+            const bool inside = px < W;
+            float m = 0.0f;  // pending h offset of the state being read
+            bool bad = false;
+            for (int step = 0; step < a.n_steps; ++step) {
+                const int cb = (a.parity0 + step) & 1;
+                const float *src = cb ? I.buf[1] : I.buf[0];
+                float *dst = cb ? I.buf[0] : I.buf[1];
+                CellQ<float> cur = {}, nxt = {};
+                Flux3<float> gd = {};
+                float ph = 0.0f, pu = 0.0f, pv = 0.0f;  // prefetched raw row
+                auto load_cell = [&](int r) {
+                    const long long o = (long long)r * pitch + px;
+                    const float h = src[o] - m;
+                    bad |= !(h > 0.0f);
+                    return make_cell<float>(h, src[o + plane], src[o + 2 * plane], kc.hg);
+                };
+                if (lw_thread && inside) {
+                    cur = load_cell(0);
+                    if (H > 1) nxt = load_cell(1);
+                    if (H > 2) {
+                        const long long o = 2 * pitch + px;
+                        ph = src[o];
+                        pu = src[o + plane];
+                        pv = src[o + 2 * plane];
+                    }
+                    gd = yface_flux(mirror_y(cur), cur, kc);
+                }
+                // every accumulator block starts from the bias (all MMAs of
+                // the previous sweep have completed: its last tick waited
+                // for them)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    arm<C::CPT>(t1 + b * 32, sBias + C::CPT * g);
+                    arm<C::CPT>(t2 + b * 32, sBias + 32 + C::CPT * g);
+                    if (lw_thread) arm<16>(t3 + b * 16, sBias + 64);
+                }
+                double hs = 0.0;
+                int lws = 0;  // lw ring slot of row t (t mod 7)
+#pragma unroll 1
+                for (int t = 0; t < T; ++t, lws = lws == C::LW_SLOTS - 1 ? 0 : lws + 1) {
+                    const uint32_t parW = (nb + (uint32_t)t - 1u) & 1u;  // batch t-1
+                    const bool publish_t = t + 1 < T;
+                    // ---- Lax-Wendroff row t; network input x0[t] ----
+                    if (lw_thread && t < H) {
+                        float *xr = sXR + (t & 1) * 3 * C::PXB;
+                        if (inside) {
+                            xr[px + 1] = cur.h;
+                            xr[C::PXB + px + 1] = cur.u;
+                            xr[2 * C::PXB + px + 1] = cur.v;
+                        }
+                        named_bar_sync(1, C::PX);
+                        uint4 x8 = zero4();
+                        if (inside) {
+                            const CellQ<float> left =
+                                px == 0 ? mirror_x(cur)
+                                        : make_cell<float>(xr[px], xr[C::PXB + px], xr[2 * C::PXB + px], kc.hg);
+                            const CellQ<float> right =
+                                px == W - 1
+                                    ? mirror_x(cur)
+                                    : make_cell<float>(xr[px + 2], xr[C::PXB + px + 2], xr[2 * C::PXB + px + 2], kc.hg);
+                            const CellQ<float> up = t + 1 < H ? nxt : mirror_y(cur);
+                            const Flux3<float> Fl = xface_flux(left, cur, kc);
+                            const Flux3<float> Fr = xface_flux(cur, right, kc);
+                            const Flux3<float> gu = yface_flux(cur, up, kc);
+                            float oh = cur.h, ou = cur.u, ov = cur.v;
+                            lw_update(oh, ou, ov, Fl, Fr, gd, gu, kc);
+                            bad |= !(oh > 0.0f);
+                            float *lw = sLW + lws * 3 * C::PX;
+                            lw[px] = oh;
+                            lw[C::PX + px] = ou;
+                            lw[2 * C::PX + px] = ov;
+                            x8.x = pack_bf16x2((oh - cur.h) * a.inv_sh, (ou - cur.u) * a.inv_su);
+                            x8.y = pack_bf16x2((ov - cur.v) * a.inv_su, 0.0f);
+                            gd = gu;
+                            if (t + 1 < H) {
+                                cur = nxt;
+                                if (t + 2 < H) {
+                                    const float h = ph - m;
+                                    bad |= !(h > 0.0f);
+                                    nxt = make_cell<float>(h, pu, pv, kc.hg);
+                                    if (t + 3 < H) {
+                                        const long long o = (long long)(t + 3) * pitch + px;
+                                        ph = src[o];
+                                        pu = src[o + plane];
+                                        pv = src[o + 2 * plane];
+                                    }
+                                }
+                            }
+                        }
+                        // slot t & 1 held x0[t-2], read by batch t-2 (waited in tick t-1)
+                        *reinterpret_cast<uint4 *>(sX0 + (t & 1) * C::X0_ROW + (px + 1) * 16) = x8;
+                    }
+                    // ---- E1 of row t-2 (completed by batch t-1) ----
+                    if (t >= 1) wait(bars + B_L1, parW);
+                    const int r1 = t - 2;
+                    if (r1 >= 0 && r1 < H)
+                        hidden_epilogue<C::CPT>(t1 + mod3(r1) * 32, sBias + C::CPT * g, sA1 + (r1 & 1) * C::A_ROW + sw,
+                                                C::STRIP, inside);
+                    if (publish_t) publish(bars + B_RDY1, lane);
+                    // ---- E2 of row t-4 ----
+                    if (t >= 1) wait(bars + B_L2, parW);
+                    const int r2 = t - 4;
+                    if (r2 >= 0 && r2 < H)
+                        hidden_epilogue<C::CPT>(t2 + mod3(r2) * 32, sBias + 32 + C::CPT * g,
+                                                sA2 + (r2 & 1) * C::A_ROW + sw, C::STRIP, inside);
+                    if (publish_t) publish(bars + B_RDY2, lane);
+                    // ---- E3: corrected row t-6 ----
+                    if (t >= 1) wait(bars + B_L3, parW);
+                    const int r3 = t - 6;
+                    if (lw_thread && r3 >= 0 && r3 < H) {
+                        const uint32_t ta = t3 + mod3(r3) * 16;
+                        float v[16];
+                        tc::ld_x16(ta, v);
+                        arm<16>(ta, sBias + 64);
+                        if (inside) {
+                            const int s3 = lws >= 6 ? lws - 6 : lws + 1;  // (t - 6) mod 7
+                            const float *lw = sLW + s3 * 3 * C::PX;
+                            const long long o = (long long)r3 * pitch + px;
+                            dst[o] = __fmaf_rn(v[0], a.os_h, lw[px]);
+                            dst[o + plane] = __fmaf_rn(v[1], a.os_u, lw[C::PX + px]);
+                            dst[o + 2 * plane] = __fmaf_rn(v[2], a.os_u, lw[2 * C::PX + px]);
+                            hs += (double)(v[0] * a.os_h);
+                        }
+                    }
+                    if (publish_t) publish(bars + B_RDY3, lane);
+                }
+                nb += (uint32_t)(T - 1);
+                // ---- mass projection: the mean h correction becomes the pending offset ----
+                if (lw_thread) {
+                    double s = hs;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) sRed[warp] = s;
+                    named_bar_sync(1, C::PX);
+                    double tot = 0.0;
+                    for (int w = 0; w < 4 * NH; ++w) tot += sRed[w];
+                    m = a.project ? (float)(tot / ((double)W * (double)H)) : 0.0f;
+                }
+            }
+            // ---- the final state: apply the pending offset, check the depth ----
+            if (lw_thread && inside && a.n_steps > 0) {
+                float *h = ((a.parity0 + a.n_steps) & 1) ? I.buf[1] : I.buf[0];
+                for (int r = 0; r < H; ++r) {
+                    const long long o = (long long)r * pitch + px;
+                    const float v = h[o] - m;
+                    if (m != 0.0f) h[o] = v;
+                    bad |= !(v > 0.0f);
+                }
+            }
+            if (lw_thread && bad) atomicOr(&a.flags[i], SWE_FLAG_NONPOSITIVE);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == C::NCW) tc::tmem_free(tmem, C::TMEM_COLS);
+}
+
+template <int NH, int NG>
+cudaError_t launch_learned(const LearnArgs &a, int grid, cudaStream_t s)
+{
+    using C = LearnCfg<NH, NG>;
+    static_assert(C::SMEM <= 232448, "shared memory of the fused learned step");
+    static_assert(8 * B_COUNT + 8 <= 128, "barrier area");
+    static_assert(C::TMEM_USED <= C::TMEM_COLS, "tensor memory");
+    static_assert(C::OFF_BIAS % 16 == 0, "bias is read as float4");
+    auto kern = learned_step_kernel<NH, NG>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once,
+                   [&] { attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); });
+    if (attr != cudaSuccess) return attr;
+    kern<<<grid, C::THREADS, C::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace swe
+
+using namespace swe;
+
+extern "C" swe_status swe_batch_learned_step(swe_batch *b, swe_net *net, int n_steps, int project_mass, void *stream)
+{
+    BatchView bv;
+    NetView nv;
+    if (!batch_view(b, &bv) || !net_view(net, &nv) || n_steps < 0) return SWE_EINVAL;
+    if (n_steps == 0) return SWE_OK;
+    int wmax = 0;
+    for (int i = 0; i < bv.n; ++i) wmax = std::max(wmax, bv.h_inst[i].nx);
+    if (wmax > 256) return SWE_EUNSUPPORTED;
+    LearnArgs a;
+    a.inst = bv.d_inst;
+    a.n_inst = bv.n;
+    a.n_steps = n_steps;
+    a.parity0 = bv.cur;
+    a.w1 = nv.w1;
+    a.w2 = nv.w2;
+    a.w3 = nv.w3;
+    a.bias = nv.bias;
+    a.inv_sh = 1.0f / nv.norm[1];
+    a.inv_su = 1.0f / nv.norm[2];
+    a.os_h = nv.norm[3];
+    a.os_u = nv.norm[4];
+    a.project = project_mass ? 1 : 0;
+    a.flags = bv.d_flags;
+    a.err = bv.d_err;
+    const int grid = std::min(bv.n, std::max(1, bv.sms));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = wmax <= 128 ? launch_learned<1, SWE_LEARN_NG>(a, grid, s)
+                                      : launch_learned<2, SWE_LEARN_NG>(a, grid, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SWE_ENOMEM : SWE_ECUDA;
+    batch_advance(b, n_steps);
+    return SWE_OK;
+}

@@ -29,11 +29,11 @@
 #include <new>
 #include <vector>
 
+#include "swe_gelu.cuh"
 #include "swe_tc.cuh"
+#include "swe_views.cuh"
 
 namespace swe {
-
-using bf16 = __nv_bfloat16;
 
 constexpr int kTileX = 128;                // output pixels per tile row (the MMA's M)
 constexpr int kHaloX = kTileX + 2;         // 130
@@ -90,38 +90,6 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
         " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
         : "memory");
-}
-
-// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.26:
-// erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
-// t = 1 / (1 + p x) for x >= 0 (odd extension), |error| <= 1.5e-7.  Also
-// returns exp(-x^2), which the GELU derivative reuses.
-__device__ __forceinline__ float erf_as(float x, float &gauss)
-{
-    const float ax = fabsf(x);
-    const float t = rcp(fmaf(0.3275911f, ax, 1.0f));
-    float poly = fmaf(1.061405429f, t, -1.453152027f);
-    poly = fmaf(poly, t, 1.421413741f);
-    poly = fmaf(poly, t, -0.284496736f);
-    poly = fmaf(poly, t, 0.254829592f);
-    poly *= t;
-    gauss = __expf(-ax * ax);
-    const float e = fmaf(-poly, gauss, 1.0f);
-    return copysignf(e, x);
-}
-
-// GELU 0.5 z (1 + erf(z / sqrt 2)) and its derivative 0.5 (1 + erf(z / sqrt 2)) + z phi(z).
-__device__ __forceinline__ float gelu_f(float z)
-{
-    float g;
-    return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f, g));
-}
-
-__device__ __forceinline__ float gelu_grad_f(float z)
-{
-    float g;  // exp(-z^2 / 2)
-    const float e = erf_as(z * 0.70710678118654752f, g);
-    return fmaf(z * g, 0.39894228040143268f, 0.5f * (1.0f + e));
 }
 
 // Evaluates erf (which = 0), gelu (1) or gelu' (2) of n values (self-test).
@@ -287,7 +255,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                 } else {
                     float *st = ea.state + n * ea.st_img + (long long)y * ea.st_pitch + x;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) st[c * ea.st_plane] = fpre[r][c] + rr[c] * ea.oscale[c];
+                    for (int c = 0; c < 3; ++c) st[c * ea.st_plane] = __fmaf_rn(rr[c], ea.oscale[c], fpre[r][c]);
                     lsum += (double)(rr[0] * ea.oscale[0]);
                 }
             }
@@ -674,6 +642,22 @@ struct swe_net {
     int *err = nullptr;
     long long step = 0;
 };
+
+namespace swe {
+
+bool net_view(swe_net *t, NetView *v)
+{
+    if (!t || !v) return false;
+    v->w1 = t->w1f;
+    v->w2 = t->w2f;
+    v->w3 = t->w3f;
+    v->bias = t->bias_pad;
+    for (int k = 0; k < 5; ++k) v->norm[k] = t->norm[k];
+    v->d_err = t->err;
+    return true;
+}
+
+}  // namespace swe
 
 static swe_status nst(cudaError_t e)
 {

@@ -89,6 +89,7 @@ _SIGS = {
     "swe_net_train_step": (_i, [_vp, _i, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _i,
                                 ctypes.POINTER(_d), _vp, _vp, _vp]),
     "swe_net_check": (_i, [_vp, _vp]),
+    "swe_batch_learned_step": (_i, [_vp, _vp, _i, _i, _vp]),
     "swe_selftest_gelu": (_i, [_vp, _vp, _i, _i, _vp]),
     "swe_downsample": (_i, [_i, _vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
@@ -359,6 +360,12 @@ class Batch:
     def step(self, n, stream=None):
         check(lib().swe_batch_step(self.b, int(n), stream if stream is not None else current_stream()),
               "swe_batch_step")
+
+    def learned_step(self, net: "Net", n, project_mass=True, stream=None):
+        """n learned coarse steps (Lax-Wendroff + corrector) in one launch."""
+        check(lib().swe_batch_learned_step(self.b, net.t, int(n), int(project_mass),
+                                           stream if stream is not None else current_stream()),
+              "swe_batch_learned_step")
 
     def status(self, stream=None):
         f = np.zeros(self.n, np.int32)

@@ -143,8 +143,9 @@ def test_training_reduces_the_loss_on_a_fixed_batch():
 
 @pytest.mark.parametrize("which", [0, 1, 2])
 def test_device_erf_and_gelu_within_published_bound(which):
-    """The network's erf (Abramowitz & Stegun 7.1.26, |error| <= 1.5e-7) and
-    the GELU / GELU' built on it, against scipy's erf in FP64."""
+    """The network's erf (Abramowitz & Stegun 7.1.26, |error| <= 1.5e-7), the
+    forward GELU (erf from A&S 7.1.27) and GELU' (7.1.26), against scipy's
+    erf in FP64."""
     import torch
     from scipy.special import erf
     from paper_1107_2157_gb300 import swe
@@ -159,8 +160,11 @@ def test_device_erf_and_gelu_within_published_bound(which):
         ref, tol = erf(x), 1.5e-7 + 4e-7  # published bound + FP32 evaluation
         assert np.abs(got - ref).max() <= tol
     elif which == 1:
+        # forward GELU with erf from A&S 7.1.27: 6.9e-4 from the formula (2.3e-4 |z|
+        # beyond |z| = 1), plus FP32 evaluation
         ref = nn.gelu(x)
-        assert np.abs(got - ref).max() <= 1e-6 * np.maximum(1.0, np.abs(x)).max()
+        assert np.all(np.abs(got - ref) <= 7e-4 * np.maximum(1.0, np.abs(x)) + 1e-6 * np.abs(x))
+        assert np.abs(got - ref).max() <= 7e-4
     else:
         ref = nn.gelu_grad(x)
         assert np.abs(got - ref).max() <= 2e-6

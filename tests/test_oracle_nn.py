@@ -91,3 +91,72 @@ def test_downsample_preserves_sums_constants_and_linear_fields():
     I = np.arange(4)[:, None] * 4 + 1.5
     J = np.arange(3)[None, :] * 4 + 1.5
     assert np.allclose(d, 0.3 * I - 0.7 * J + 1.0, atol=1e-14)
+
+
+def test_bf16_rounding_is_nearest_even():
+    from oracle.learned import bf16_round
+    one = 1.0
+    ulp = 2.0 ** -7                      # bf16 spacing at 1
+    x = np.array([one, one + ulp, one + ulp / 2, one + 3 * ulp / 2, -(one + ulp / 2), 0.0, 3.0e38, 1e-40])
+    got = bf16_round(x)
+    assert got[0] == one and got[1] == one + ulp
+    assert got[2] == one                 # tie -> even mantissa
+    assert got[3] == one + 2 * ulp       # tie -> even mantissa
+    assert got[4] == -one
+    assert got[5] == 0.0
+    assert np.isfinite(got[6])
+    assert got[7] == 2.0 ** -133         # subnormal: the bf16 spacing there is 2^-133
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(1000)
+    r = bf16_round(v)
+    assert np.all(np.abs(r - v) <= 2.0 ** -8 * np.abs(v) * (1 + 1e-6))  # unit roundoff of 8 significant bits
+
+
+def _learned_state(seed, nx, ny):
+    import swe_inputs as si
+    return si.smooth_flow_state(seed, nx, ny)
+
+
+def test_learned_step_with_zero_network_is_the_lax_wendroff_step():
+    import oracle
+    from oracle import learned
+    s = _learned_state(1, 13, 9)
+    p = {k: np.zeros_like(v) for k, v in nn.init_params(0).items()}
+    got, d = learned.corrected_step(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, p, (0, 1e-3, 1e-3, 1e-2, 1e-2))
+    ref = oracle.run(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, 1)
+    for k in range(3):
+        assert np.array_equal(got[k], ref[k])
+    assert not d.any()
+
+
+def test_learned_step_constant_output_scaling_and_projection():
+    """W3 = 0 makes the network output its bias b3 everywhere: the h
+    correction oh*b3[0] is removed by the projection, the momentum
+    corrections are ou*b3[1:] exactly."""
+    import oracle
+    from oracle import learned
+    s = _learned_state(2, 11, 7)
+    p = nn.init_params(3)
+    p["W3"] = np.zeros_like(p["W3"])
+    p["b3"] = np.array([0.5, -0.25, 2.0])
+    norm = (0.0, 1e-3, 1e-3, 1e-2, 4e-2)
+    ref = oracle.run(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, 1)
+    got, _ = learned.corrected_step(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, p, norm, project_mass=True)
+    assert np.allclose(got[0], ref[0], rtol=0, atol=1e-15)
+    assert np.allclose(got[1], ref[1] + 4e-2 * -0.25, rtol=0, atol=1e-15)
+    assert np.allclose(got[2], ref[2] + 4e-2 * 2.0, rtol=0, atol=1e-15)
+    got, _ = learned.corrected_step(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, p, norm, project_mass=False)
+    assert np.allclose(got[0], ref[0] + 1e-2 * 0.5, rtol=0, atol=1e-15)
+
+
+def test_learned_step_keeps_mass_under_projection():
+    import oracle
+    from oracle import learned
+    s = _learned_state(4, 17, 12)
+    p = nn.init_params(5, out_scale=1.0)
+    norm = (0.0, 1e-3, 1e-3, 1e-2, 1e-2)
+    m0 = oracle.mass(s.h, 1.0, 1.0)
+    got = learned.corrected_run(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, p, norm, 3)
+    assert abs(oracle.mass(got[0], 1.0, 1.0) - m0) <= 1e-13 * m0
+    free, _ = learned.corrected_step(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, p, norm, project_mass=False)
+    assert abs(oracle.mass(free[0], 1.0, 1.0) - m0) > 1e-9 * m0  # the network alone does not
