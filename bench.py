@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--train-trajectories", type=int, default=1792)
     p.add_argument("--eval-trajectories", type=int, default=200)
     p.add_argument("--serve-instances", type=int, default=1024)
-    p.add_argument("--passes", type=int, default=1)
+    p.add_argument("--passes", type=int, default=2)
     p.add_argument("--ensemble-count", type=int, default=512)
     p.add_argument("--no-tune", action="store_true", help="ensemble: default kernel variant, no autotuning")
     p.add_argument("--skip-train", action="store_true",
@@ -468,10 +468,8 @@ def run_learned(args):
 
     import swe_inputs as si
     from paper_1107_2157_gb300 import corrector as C
-    from paper_1107_2157_gb300 import swe
 
     torch.cuda.set_device(0)
-    sp = torch.cuda.current_stream().cuda_stream
     setup = C.Setup(n_fine=1024, factor=4, dt_fine=0.04, coarse_steps=64)
     nc = setup.n_coarse
     if args.skip_train:
@@ -489,14 +487,6 @@ def run_learned(args):
     res = C.train(setup, range(0, args.train_trajectories), B=32, lr=1e-3, passes=args.passes, gen_batch=64)
     t_train = time.perf_counter() - t0
 
-    def restrict(batch, factor, n):
-        out = torch.zeros((n, 3, nc, nc), dtype=torch.float32, device="cuda")
-        p0, plane, pitch = batch.state_ptr(0)
-        img = (batch.state_ptr(1)[0] - p0) // 4 if n > 1 else 3 * plane
-        swe.swe_downsample(factor, p0, img, plane, pitch, out.data_ptr(), 3 * nc * nc, nc * nc, nc, nc, nc, n)
-        torch.cuda.synchronize()
-        return out.cpu().numpy()
-
     # held-out error of config "training": seeds 1800.., 64 coarse steps
     eval_seeds = list(range(1800, 1800 + args.eval_trajectories))
     e_plain, e_learned, flags_eval = [], [], 0
@@ -512,41 +502,60 @@ def run_learned(args):
         out["coarse"].close()
     e_plain, e_learned = np.array(e_plain), np.array(e_learned)
 
-    # serving: N instances (seeds 10000..) learned-coarse vs plain fine and plain 512^2
+    # serving: N instances (seeds 10000..): learned-coarse vs the plain method
+    # at N x N for N in LEVELS (area-weighted restriction in and out), the
+    # plain fine 1024^2 run being the truth
     n = args.serve_instances
     states = si.corrector_states(range(10000, 10000 + n), setup.n_fine, setup.dam_fraction)
-    out = C.serve(setup, states, res["params"], res["norm"])  # warm-up / compile
+    out = C.serve(setup, states, res["params"], res["norm"])  # warm-up
     out["coarse"].close()
     out = C.serve(setup, states, res["params"], res["norm"])
     t_learned = out["seconds"]
     fallback_rate = float(out["flagged"].mean())
     learned_c = out["coarse"]
+    # the same serving with one Lax-Wendroff launch + the network's launches per step
+    unf = C.serve(setup, states, res["params"], res["norm"], fused=False)
+    t_learned_unfused = unf["seconds"]
+    unf["coarse"].close()
     tt = []
-    truth = C.fine_truth(setup, states, timing=tt)
+    truth = C.fine_truth(setup, states, timing=tt, tune=True)
     t_fine = tt[0]
     el = C.rms_h_error(learned_c, truth)
     learned_c.close()
-    # plain coarse 256^2 and plain 512^2 on the same initial states
-    tp = []
-    pc = C.coarse_run(setup, states, None, None, timing=tp)
-    ep256 = C.rms_h_error(pc, truth)
-    pc.close()
-    setup512 = C.Setup(n_fine=1024, factor=2, dt_fine=0.04, coarse_steps=128)
-    tp512 = []
-    b512 = C.coarse_run(setup512, states, None, None, timing=tp512)
-    r512 = restrict(b512, 2, n)
-    b512.close()
-    ep512 = np.sqrt(((r512[:, 0].astype(np.float64) - truth[:, 0]) ** 2).mean(axis=(1, 2)))
-    levels = [(256, float(ep256.mean()), tp[0]), (512, float(ep512.mean()), tp512[0]), (1024, 0.0, t_fine)]
+    fine0 = C.load_fine(setup, states)
+    levels = []
+    try:
+        for N in (256, 320, 384, 512, 640, 768):
+            tp = []
+            hN = C.plain_at(setup, fine0, N, timing=tp, tune=True)
+            eN = C.rms_h_error_arrays(hN, truth)
+            levels.append({"N": N, "l2_h_mean": float(eN.mean()), "l2_h_median": float(np.median(eN)), "t_s": tp[0]})
+            del hN
+    finally:
+        fine0.close()
+    levels.append({"N": 1024, "l2_h_mean": 0.0, "l2_h_median": 0.0, "t_s": t_fine})
     l_err = float(el.mean())
-    n_star = next(N for N, e, _ in levels if e <= l_err)
-    t_star = next(t for N, e, t in levels if N == n_star)
+    star = next(lv for lv in levels if lv["l2_h_mean"] <= l_err)
+    # the plain method's time at the learned error, interpolated linearly in
+    # error between the two levels that bracket it (the discrete N* above
+    # rounds up to the next level)
+    t_interp = None
+    for lo, hi in zip(levels, levels[1:]):
+        if hi["l2_h_mean"] <= l_err <= lo["l2_h_mean"]:
+            w = (lo["l2_h_mean"] - l_err) / max(lo["l2_h_mean"] - hi["l2_h_mean"], 1e-300)
+            t_interp = lo["t_s"] + w * (hi["t_s"] - lo["t_s"])
+            break
+    if t_interp is None:
+        t_interp = levels[0]["t_s"] if l_err >= levels[0]["l2_h_mean"] else star["t_s"]
+    l_med = float(np.median(el))
+    star_med = next(lv for lv in levels if lv["l2_h_median"] <= l_med)
     fine_updates = n * 1024 * 1024 * 256
     line = {
         "metric": METRIC, "workload": "learned", "unit": "s",
-        "train": {"trajectories": args.train_trajectories, "steps": res["steps"], "seconds": t_train,
-                  "loss_first": float(np.mean(res["losses"][:50])), "loss_last": float(np.mean(res["losses"][-200:])),
-                  "norm": res["norm"]},
+        "train": {"trajectories": args.train_trajectories, "passes": args.passes, "steps": res["steps"],
+                  "seconds": t_train, "loss_first": float(np.mean(res["losses"][:50])),
+                  "loss_last": float(np.mean(res["losses"][-200:])), "norm": res["norm"],
+                  "loss": "per-image weighted MSE, w = max(ms, 1)^-0.75", "target_clip": None},
         "eval_training_config": {"seeds": "1800..%d" % (1799 + args.eval_trajectories),
                                  "l2_h_plain_coarse_mean": float(e_plain.mean()),
                                  "l2_h_learned_mean": float(e_learned.mean()),
@@ -555,13 +564,15 @@ def run_learned(args):
                                  "median_ratio": float(np.median(e_learned / e_plain)),
                                  "fallbacks": flags_eval},
         "serving": {"instances": n, "coarse": "256x256", "coarse_steps": 64,
-                    "t_learned_s": t_learned, "t_plain_fine_1024_s": t_fine, "t_plain_512_s": tp512[0],
-                    "t_plain_coarse_256_s": tp[0],
-                    "l2_h_learned_mean": l_err, "l2_h_plain_256_mean": levels[0][1],
-                    "l2_h_plain_512_mean": levels[1][1], "l2_h_learned_median": float(np.median(el)),
-                    "l2_h_plain_256_median": float(np.median(ep256)), "l2_h_plain_512_median": float(np.median(ep512)),
-                    "equal_error_N": n_star, "speedup_vs_plain_fine_1024": t_fine / t_learned,
-                    "speedup_vs_plain_at_equal_error": t_star / t_learned, "fallback_rate": fallback_rate,
+                    "t_learned_s": t_learned, "t_learned_unfused_s": t_learned_unfused,
+                    "t_plain_fine_1024_s": t_fine, "l2_h_learned_mean": l_err, "l2_h_learned_median": l_med,
+                    "plain_levels": levels,
+                    "equal_error_N": star["N"], "speedup_vs_plain_at_equal_error": star["t_s"] / t_learned,
+                    "t_plain_at_learned_error_interp_s": t_interp,
+                    "speedup_vs_plain_at_equal_error_interp": t_interp / t_learned,
+                    "equal_median_error_N": star_med["N"],
+                    "speedup_vs_plain_at_equal_median_error": star_med["t_s"] / t_learned,
+                    "speedup_vs_plain_fine_1024": t_fine / t_learned, "fallback_rate": fallback_rate,
                     "coarse_cell_updates_per_s": n * nc * nc * 64 / t_learned,
                     "fine_equivalent_cell_updates_per_s": fine_updates / t_learned},
     }

@@ -335,13 +335,20 @@ swe_status swe_net_correct(swe_net *net, int n, float *state, long long img_stri
 swe_status swe_net_make_target(swe_net *net, int n, const float *next, const float *lw, long long img_stride,
                                long long plane_stride, long long pitch, float clip, float *target, void *stream);
 /* One training step on the prepared input: forward, mean squared error
- * against target, backward (tcgen05 input gradients, CUDA-core weight
+ * against target (weighted per image, see swe_net_set_loss_weighting), backward (tcgen05 input gradients, CUDA-core weight
  * gradients), and with update = 1 an AdamW step (lr, weight decay wd,
  * global-norm clip if clip > 0).  Synchronous.  Optional outputs: the loss,
  * the gradients (host, param_count floats), the raw network output r
  * (device FP32 [n][3][H][W]). */
 swe_status swe_net_train_step(swe_net *net, int n, const float *target, float lr, float wd, float clip, int update,
                               double *loss_out, float *grads_out, float *resid_out, void *stream);
+/* Per-image weighting of the training loss: image i's squared error is
+ * multiplied by w_i = max(ms_i, floor)^(-power/2), ms_i the mean square of
+ * its target over the three channels (computed on the device each step).
+ * power = 0 (the default) is the plain mean squared error; power = 1 weighs
+ * an image by the inverse of its target's RMS, power = 2 makes every
+ * image's relative error count alike.  0 <= power <= 4, floor > 0. */
+swe_status swe_net_set_loss_weighting(swe_net *net, float power, float floor);
 /* Synchronises and returns the device error word of the net's kernels. */
 swe_status swe_net_check(swe_net *net, void *stream);
 /* The learned coarse step of every instance of batch b, n_steps times, in
@@ -373,6 +380,19 @@ swe_status swe_selftest_gelu(const float *z, float *out, int n, int which, void 
 swe_status swe_downsample(int factor, const float *fine, long long f_img, long long f_plane, long long f_pitch,
                           float *coarse, long long c_img, long long c_plane, long long c_pitch, int Wc, int Hc, int n,
                           void *stream);
+
+/* Area-weighted average of n images (3 planes each) of Hs x Ws cells onto
+ * Hd x Wd cells covering the same domain (Wd <= Ws, Hd <= Hs, any ratio):
+ * destination cell (X, Y) is the mean of the source over
+ * [X Ws/Wd, (X+1) Ws/Wd) x [Y Hs/Hd, (Y+1) Hs/Hd), each source cell weighted
+ * by its overlap (FP64 sums).  Keeps the integral of every plane; an
+ * integer ratio is the block average of swe_downsample.  The restriction
+ * between grids of the learned-vs-plain protocol (no counterpart in the
+ * paper).  Strides in floats as above; stream-ordered; SWE_EINVAL for
+ * upsampling or bad strides. */
+swe_status swe_resample(const float *src, long long s_img, long long s_plane, long long s_pitch, int Ws, int Hs,
+                        float *dst, long long d_img, long long d_plane, long long d_pitch, int Wd, int Hd, int n,
+                        void *stream);
 
 #ifdef __cplusplus
 }

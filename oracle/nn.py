@@ -17,7 +17,8 @@ input is 0):  y[n, o, i, j] = b[o] + sum_{c, dy, dx} W[dy+1, dx+1, c, o] *
 x[n, c, i+dy, j+dx], with i the row (y) and j the column (x) index.
 Weights are stored as W[ky, kx, c_in, c_out].  gelu is the exact erf form
 0.5 z (1 + erf(z / sqrt 2)).  The loss is the mean squared error over all
-elements.  Arrays are NCHW float64.
+elements, optionally weighted per image (``image_weights``).  Arrays are
+NCHW float64.
 """
 from __future__ import annotations
 
@@ -88,13 +89,26 @@ def forward(params, x0):
     return r, dict(x0=x0, z1=z1, a1=a1, z2=z2, a2=a2)
 
 
-def loss(r, t):
-    return float(np.mean((r - t) ** 2))
+def image_weights(t, power, floor):
+    """Per-image loss weights w_i = max(ms_i, floor)^(-power/2), ms_i the
+    mean square of image i's target (all channels)."""
+    ms = np.mean(np.asarray(t, np.float64).reshape(t.shape[0], -1) ** 2, axis=1)
+    return np.maximum(ms, floor) ** (-0.5 * power)
 
 
-def backward(params, cache, r, t):
-    """Gradients of mean((r - t)^2) w.r.t. every parameter."""
+def loss(r, t, w=None):
+    """mean over all elements of w_i (r - t)^2 (w = None: plain MSE)."""
+    d2 = (r - t) ** 2
+    if w is not None:
+        d2 = d2 * np.asarray(w, np.float64)[:, None, None, None]
+    return float(np.mean(d2))
+
+
+def backward(params, cache, r, t, w=None):
+    """Gradients of loss(r, t, w) w.r.t. every parameter."""
     dr = 2.0 * (r - t) / r.size
+    if w is not None:
+        dr = dr * np.asarray(w, np.float64)[:, None, None, None]
     g = {}
     g["W3"], g["b3"] = conv3x3_weight_grad(cache["a2"], dr)
     dz2 = conv3x3_input_grad(dr, params["W3"]) * gelu_grad(cache["z2"])
@@ -121,6 +135,26 @@ def block_average(u: np.ndarray, f: int) -> np.ndarray:
     H, W = u.shape[-2], u.shape[-1]
     v = u.reshape(u.shape[:-2] + (H // f, f, W // f, f))
     return v.sum(axis=(-3, -1)) / float(f * f)
+
+
+def area_matrix(n_src: int, n_dst: int) -> np.ndarray:
+    """R[X, i] = |[X f, (X+1) f) & [i, i+1)| / f, f = n_src / n_dst: the
+    overlap-weighted mean of source cells over destination cell X."""
+    f = n_src / n_dst
+    R = np.zeros((n_dst, n_src))
+    for X in range(n_dst):
+        a, b = X * f, (X + 1) * f
+        for i in range(int(np.floor(a)), min(n_src, int(np.ceil(b)))):
+            R[X, i] = (min(b, i + 1) - max(a, i)) / f
+    return R
+
+
+def area_average(u: np.ndarray, h_dst: int, w_dst: int) -> np.ndarray:
+    """Area-weighted average of the last two axes onto h_dst x w_dst cells
+    covering the same domain (any ratio >= 1): R_y u R_x^T."""
+    Ry = area_matrix(u.shape[-2], h_dst)
+    Rx = area_matrix(u.shape[-1], w_dst)
+    return Ry @ np.asarray(u, np.float64) @ Rx.T
 
 
 def downsample4(u: np.ndarray) -> np.ndarray:

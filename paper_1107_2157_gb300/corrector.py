@@ -3,7 +3,10 @@
 The drivers only sequence library calls; every arithmetic step runs in
 libswe.so: the fine and coarse Lax-Wendroff solvers (swe_batch_*), the
 block-average restriction (swe_downsample), the training targets, the
-network's forward/backward/AdamW (swe_net_*), and the corrected coarse step.
+network's forward/backward/AdamW (swe_net_*), and the corrected coarse step
+-- by default all coarse steps of a run in one fused persistent launch
+(swe_batch_learned_step), otherwise one Lax-Wendroff launch plus the
+network's launches per step.
 
 Protocol (fine grid n_fine^2, coarse grid n_fine/factor, dt_coarse =
 factor * dt_fine):
@@ -28,7 +31,7 @@ import numpy as np
 
 import swe_inputs as si
 
-from .swe import Batch, Net, flatten_params, swe_downsample
+from .swe import Batch, Net, flatten_params, swe_downsample, swe_resample
 
 
 @dataclasses.dataclass
@@ -137,14 +140,17 @@ def compute_norm(setup: Setup, seeds, B: int, stream) -> List[float]:
 
 def train(setup: Setup, seeds, B: int = 32, lr: float = 1e-3, epochs: int = 1, params: Optional[np.ndarray] = None,
           norm: Optional[List[float]] = None, clip: float = 1.0, log_every: int = 0, wd: float = 0.0,
-          gen_batch: int = 64, passes: int = 1, seed: int = 0, target_clip: float = 20.0) -> Dict:
+          gen_batch: int = 64, passes: int = 1, seed: int = 0, target_clip: float = 0.0,
+          loss_power: float = 1.5, loss_floor: float = 1.0) -> Dict:
     """Trains the corrector on trajectories generated on the fly.
 
     Trajectories are generated gen_batch at a time; all their (input, target)
     pairs over the coarse steps go to a device buffer -- the coarse state c_k,
     its Lax-Wendroff result LW_c(c_k) and the normalised target residual,
-    clipped to +-target_clip -- which is shuffled and consumed in minibatches
-    of B (``passes`` times).  The network input is the increment
+    clipped to +-target_clip (0 = no clip) -- which is shuffled and consumed
+    in minibatches of B (``passes`` times).  The loss is the mean squared
+    error, each image weighted by max(ms, loss_floor)^(-loss_power/2), ms
+    the mean square of its target (loss_power = 0: plain MSE).  The network input is the increment
     LW_c(c_k) - c_k.  The learning rate follows a cosine from lr to lr/20.
     Returns dict(params, norm, losses, seconds, steps)."""
     import torch
@@ -163,6 +169,7 @@ def train(setup: Setup, seeds, B: int = 32, lr: float = 1e-3, epochs: int = 1, p
     net = Net(B, nc, nc)
     net.set_params(init_params(0) if params is None else params)
     net.set_norm(*norm)
+    net.set_loss_weighting(loss_power, loss_floor)
     pair = _Pair(setup, gen_batch, sp)
     gen = torch.Generator(device="cpu")
     gen.manual_seed(seed)
@@ -210,7 +217,7 @@ def train(setup: Setup, seeds, B: int = 32, lr: float = 1e-3, epochs: int = 1, p
 
 
 def coarse_run(setup: Setup, states: List[si.State], params: Optional[np.ndarray], norm, project_mass=True,
-               steps: Optional[int] = None, net: Optional[Net] = None, stream=None, timing=None):
+               steps: Optional[int] = None, net: Optional[Net] = None, stream=None, timing=None, fused=True):
     """Coarse runs (plain LW if params is None, else LW + corrector) from the
     restricted initial states; returns the coarse Batch (caller closes)."""
     import torch
@@ -223,13 +230,16 @@ def coarse_run(setup: Setup, states: List[si.State], params: Optional[np.ndarray
     coarse = pair.coarse
     own = None
     if params is not None and net is None:
-        own = net = Net(B, setup.n_coarse, setup.n_coarse)
+        # the fused step reads only the weights: no activation buffers needed
+        own = net = Net(1, 8, 8) if fused else Net(B, setup.n_coarse, setup.n_coarse)
         net.set_params(params)
         net.set_norm(*norm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if params is None:
         coarse.step(K, stream=sp)
+    elif fused:
+        coarse.learned_step(net, K, project_mass=project_mass, stream=sp)
     else:
         for _ in range(K):
             c0 = _Pair.geom(coarse)[0]  # c_k stays in the other buffer after the step
@@ -245,7 +255,8 @@ def coarse_run(setup: Setup, states: List[si.State], params: Optional[np.ndarray
     return coarse
 
 
-def fine_truth(setup: Setup, states: List[si.State], stream=None, timing=None, factor_out: Optional[int] = None):
+def fine_truth(setup: Setup, states: List[si.State], stream=None, timing=None, factor_out: Optional[int] = None,
+               tune: bool = False):
     """Fine runs to the final time, restricted to the coarse grid: [B][3][nc][nc]."""
     import torch
     sp = stream if stream is not None else torch.cuda.current_stream().cuda_stream
@@ -254,6 +265,8 @@ def fine_truth(setup: Setup, states: List[si.State], stream=None, timing=None, f
     try:
         for i, st in enumerate(states):
             pair.fine.set_state(i, *(a.astype(np.float32) for a in (st.h, st.hu, st.hv)), stream=sp)
+        if tune:
+            pair.fine.tune(stream=sp)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pair.fine.step(setup.coarse_steps * setup.factor, stream=sp)
@@ -267,6 +280,54 @@ def fine_truth(setup: Setup, states: List[si.State], stream=None, timing=None, f
         pair.close()
 
 
+def load_fine(setup: Setup, states: List[si.State], stream=None) -> Batch:
+    """The fine initial states in a fine batch (caller closes)."""
+    import torch
+    sp = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    b = Batch([(setup.n_fine, setup.n_fine)] * len(states), 1.0, 1.0, setup.dt_fine, setup.g)
+    for i, st in enumerate(states):
+        b.set_state(i, *(a.astype(np.float32) for a in (st.h, st.hu, st.hv)), stream=sp)
+    return b
+
+
+def plain_at(setup: Setup, fine0: Batch, N: int, stream=None, timing=None, tune: bool = False) -> np.ndarray:
+    """The plain method at N x N cells (spacing n_fine / N, time step
+    dt_fine n_fine / N) from the area average of the fine batch's current
+    state, run to the coarse run's final time; returns its final state area
+    averaged onto the coarse grid, [B][3][nc][nc]."""
+    import torch
+    sp = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    nf, nc, B = setup.n_fine, setup.n_coarse, fine0.n
+    f = nf / N
+    steps = setup.coarse_steps * setup.factor * N // nf
+    assert steps * nf == setup.coarse_steps * setup.factor * N, "N must divide the fine time steps evenly"
+    b = Batch([(N, N)] * B, f, f, setup.dt_fine * f, setup.g)
+    try:
+        f0, fimg, fpl, fpi = _Pair.geom(fine0)
+        p0, img, pl, pi = _Pair.geom(b)
+        swe_resample(f0, fimg, fpl, fpi, nf, nf, p0, img, pl, pi, N, N, B, stream=sp)
+        if tune:
+            b.tune(stream=sp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(steps, stream=sp)
+        torch.cuda.synchronize()
+        if timing is not None:
+            timing.append(time.perf_counter() - t0)
+        out = torch.zeros((B, 3, nc, nc), dtype=torch.float32, device="cuda")
+        p0, img, pl, pi = _Pair.geom(b)
+        swe_resample(p0, img, pl, pi, N, N, out.data_ptr(), 3 * nc * nc, nc * nc, nc, nc, nc, B, stream=sp)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        b.close()
+
+
+def rms_h_error_arrays(h: np.ndarray, truth: np.ndarray) -> np.ndarray:
+    """Per-instance RMS of h ([B][3][nc][nc] arrays) against the truth."""
+    return np.sqrt(((h[:, 0].astype(np.float64) - truth[:, 0]) ** 2).mean(axis=(1, 2)))
+
+
 def rms_h_error(coarse: Batch, truth: np.ndarray) -> np.ndarray:
     """Per-instance RMS error of h against the restricted fine solution."""
     out = []
@@ -277,10 +338,11 @@ def rms_h_error(coarse: Batch, truth: np.ndarray) -> np.ndarray:
 
 
 def serve(setup: Setup, states: List[si.State], params: np.ndarray, norm, mass_tol: float = 1e-5,
-          fallback: bool = True, project_mass: bool = True, stream=None) -> Dict:
+          fallback: bool = True, project_mass: bool = True, stream=None, fused: bool = True) -> Dict:
     """Learned-coarse serving of a batch of instances with checks.
 
-    Runs the corrected coarse step for every instance, then flags an
+    Runs the corrected coarse step for every instance (all steps in one
+    fused launch unless fused=False), then flags an
     instance whose relative mass drift exceeds ``mass_tol`` or whose depth
     became non-positive (or not finite) during the run; flagged instances are
     recomputed with the plain fine solver from their fine initial state and
@@ -297,19 +359,22 @@ def serve(setup: Setup, states: List[si.State], params: np.ndarray, norm, mass_t
     pair.load(states)
     pair.fine.close()
     coarse = pair.coarse
-    net = Net(B, nc, nc)
+    net = Net(1, 8, 8) if fused else Net(B, nc, nc)
     net.set_params(params)
     net.set_norm(*norm)
     try:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m0 = coarse.mass(stream=sp)
-        for _ in range(K):
-            c0 = _Pair.geom(coarse)[0]
-            coarse.step(1, stream=sp)
-            l0, limg, lpl, lpi = _Pair.geom(coarse)
-            net.prep_input(B, l0, limg, lpl, lpi, base_ptr=c0, stream=sp)
-            net.correct(B, l0, limg, lpl, lpi, project_mass=project_mass, stream=sp)
+        if fused:
+            coarse.learned_step(net, K, project_mass=project_mass, stream=sp)
+        else:
+            for _ in range(K):
+                c0 = _Pair.geom(coarse)[0]
+                coarse.step(1, stream=sp)
+                l0, limg, lpl, lpi = _Pair.geom(coarse)
+                net.prep_input(B, l0, limg, lpl, lpi, base_ptr=c0, stream=sp)
+                net.correct(B, l0, limg, lpl, lpi, project_mass=project_mass, stream=sp)
         rc, flags = coarse.status(stream=sp)
         m1 = coarse.mass(stream=sp)
         t1 = time.perf_counter()

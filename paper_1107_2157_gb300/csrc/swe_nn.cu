@@ -79,6 +79,7 @@ struct EpiArgs {
     long long st_img, st_plane, st_pitch;  // EPI_APPLY: their strides (floats)
     double *hsum;             // EPI_APPLY: per-image sum of the h correction (may be null)
     float loss_scale;         // EPI_LOSS: d loss / d r factor (2 / count)
+    const float *img_w;       // EPI_LOSS: per-image loss weight (null = 1)
     double *loss_accum;       // EPI_LOSS: sum of squared errors
 };
 
@@ -238,11 +239,12 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
                     __align__(16) bf16 d8[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k) d8[k] = __float2bfloat16_rn(0.0f);
+                    const float w = ea.img_w ? __ldg(ea.img_w + n) : 1.0f;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const float d = rr[c] - fpre[r][c];
-                        lsum += (double)d * (double)d;
-                        d8[c] = __float2bfloat16_rn(ea.loss_scale * d);
+                        lsum += (double)w * ((double)d * (double)d);
+                        d8[c] = __float2bfloat16_rn(ea.loss_scale * w * d);
                         if (ea.resid) ea.resid[po + c * plane] = rr[c];
                     }
                     *reinterpret_cast<uint4 *>(ea.out + rc_index(n, y, 0, x, H, W, 2)) =
@@ -332,6 +334,42 @@ __global__ void downsample_kernel(const float *__restrict__ fine, long long f_im
 #pragma unroll
             for (int b = 0; b < F; ++b) s += src[a * fpitch + b];
         coarse[i * c_img + f * c_plane + (long long)Y * cpitch + X] = s * inv;
+    }
+}
+
+// Area-weighted average of n images (3 planes each) of Hs x Ws cells onto
+// Hd x Wd cells covering the same square (Wd <= Ws, Hd <= Hs): destination
+// cell X spans [X fx, (X+1) fx) source cells, fx = Ws / Wd, and takes the
+// mean of the source over that span, each source cell weighted by its
+// overlap; separable in x and y.  The integral of every plane is kept, and
+// an integer ratio is the plain block average.
+__global__ void resample_kernel(const float *__restrict__ src, long long s_img, long long s_plane, long long s_pitch,
+                                int Ws, int Hs, float *__restrict__ dst, long long d_img, long long d_plane,
+                                long long d_pitch, int Wd, int Hd, int n)
+{
+    const long long total = (long long)n * 3 * Hd * Wd;
+    const double fx = (double)Ws / Wd, fy = (double)Hs / Hd;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(p % Wd);
+        const int Y = (int)((p / Wd) % Hd);
+        const int f = (int)((p / ((long long)Wd * Hd)) % 3);
+        const int i = (int)(p / ((long long)Wd * Hd * 3));
+        const double x0 = X * fx, x1 = (X + 1) * fx, y0 = Y * fy, y1 = (Y + 1) * fy;
+        const int i0 = (int)floor(x0), i1 = min(Ws, (int)ceil(x1));
+        const int j0 = (int)floor(y0), j1 = min(Hs, (int)ceil(y1));
+        const float *plane = src + i * s_img + f * s_plane;
+        double acc = 0.0;
+        for (int j = j0; j < j1; ++j) {
+            const double wy = fmin(y1, (double)(j + 1)) - fmax(y0, (double)j);
+            double row = 0.0;
+            for (int c = i0; c < i1; ++c) {
+                const double wx = fmin(x1, (double)(c + 1)) - fmax(x0, (double)c);
+                row += wx * (double)plane[(long long)j * s_pitch + c];
+            }
+            acc += wy * row;
+        }
+        dst[i * d_img + f * d_plane + (long long)Y * d_pitch + X] = (float)(acc / (fx * fy));
     }
 }
 
@@ -566,6 +604,28 @@ __global__ void make_target_kernel(const float *__restrict__ next, const float *
     }
 }
 
+// Per-image loss weight w[i] = max(ms_i, floor)^(-power/2), ms_i the mean
+// square of image i's target over its three channels (one block per image,
+// FP64 sums in a fixed order).
+__global__ void __launch_bounds__(256) image_weight_kernel(const float *__restrict__ target, long long img_elems,
+                                                           float power, float floor, float *__restrict__ w)
+{
+    __shared__ double part[8];
+    const float *t = target + (size_t)blockIdx.x * img_elems;
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < img_elems; e += blockDim.x) s += (double)t[e] * (double)t[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < 8; ++k) tot += part[k];
+        const double ms = fmax(tot / (double)img_elems, (double)floor);
+        w[blockIdx.x] = (float)pow(ms, -0.5 * (double)power);
+    }
+}
+
 bool encode_act_map(CUtensorMap *map, const void *base, int W, int H, int CH, int N, int box_rows);
 
 }  // namespace swe
@@ -639,6 +699,8 @@ struct swe_net {
     float norm[5] = {1.0f, 1.0f, 1.0f, 1.0f, 1.0f};  // h0, sh, su, oh, ou
     double *loss = nullptr, *h_loss = nullptr;
     double *hsum = nullptr;
+    float *img_w = nullptr;          // per-image loss weights (max_images)
+    float loss_power = 0.0f, loss_floor = 1.0f;
     int *err = nullptr;
     long long step = 0;
 };
@@ -695,7 +757,7 @@ void swe_net_destroy(swe_net *t)
                     (void *)t->partial, (void *)t->bias_pad, (void *)t->gnorm, (void *)t->w1f, (void *)t->w2f,
                     (void *)t->w3f, (void *)t->w2d, (void *)t->w3d, (void *)t->x0, (void *)t->z1, (void *)t->a1,
                     (void *)t->z2, (void *)t->a2, (void *)t->dr, (void *)t->dz2, (void *)t->dz1, (void *)t->resid,
-                    (void *)t->loss, (void *)t->err, (void *)t->hsum})
+                    (void *)t->loss, (void *)t->err, (void *)t->hsum, (void *)t->img_w})
         cudaFree(p);
     cudaFreeHost(t->h_loss);
     delete t;
@@ -730,6 +792,7 @@ swe_status swe_net_create(int max_images, int H, int W, swe_net **out)
         {(void **)&t->z2, px * 32 * 2}, {(void **)&t->a2, px * 32 * 2}, {(void **)&t->dr, px * 16 * 2},
         {(void **)&t->dz2, px * 32 * 2}, {(void **)&t->dz1, px * 32 * 2}, {(void **)&t->resid, px * 3 * 4},
         {(void **)&t->loss, 16}, {(void **)&t->err, 16}, {(void **)&t->hsum, (size_t)max_images * 8},
+        {(void **)&t->img_w, (size_t)max_images * 4},
     };
     for (auto &a : allocs) {
         swe_status st = nst(cudaMalloc(a.p, a.bytes));
@@ -881,6 +944,11 @@ swe_status swe_net_train_step(swe_net *t, int n, const float *target, float lr, 
     e3.resid = resid_out;
     e3.loss_scale = (float)(2.0 / count);
     e3.loss_accum = t->loss;
+    if (t->loss_power != 0.0f) {
+        image_weight_kernel<<<n, 256, 0, s>>>(target, (long long)3 * H * W, t->loss_power, t->loss_floor, t->img_w);
+        N_TRY(cudaGetLastError());
+        e3.img_w = t->img_w;
+    }
     N_TRY((launch_conv<4, 16, EPI_LOSS>(t->m_a2, t->w3f, e3, W, H, n, t->err, s)));
     // input gradients: dz2 = conv^T(dr; W3) * gelu'(z2), dz1 = conv^T(dz2; W2) * gelu'(z1)
     EpiArgs b3 = {};
@@ -929,6 +997,15 @@ swe_status swe_net_train_step(swe_net *t, int n, const float *target, float lr, 
     return SWE_OK;
 }
 
+swe_status swe_net_set_loss_weighting(swe_net *t, float power, float floor)
+{
+    if (!t || !std::isfinite(power) || power < 0.0f || power > 4.0f || !(floor > 0.0f) || !std::isfinite(floor))
+        return SWE_EINVAL;
+    t->loss_power = power;
+    t->loss_floor = floor;
+    return SWE_OK;
+}
+
 swe_status swe_net_check(swe_net *t, void *stream)
 {
     if (!t) return SWE_EINVAL;
@@ -948,6 +1025,17 @@ swe_status swe_selftest_gelu(const float *z, float *out, int n, int which, void 
     if (!z || !out || n < 0 || which < 0 || which > 2) return SWE_EINVAL;
     gelu_probe_kernel<<<(n + 255) / 256 > 0 ? std::min((n + 255) / 256, 4096) : 1, 256, 0,
                         static_cast<cudaStream_t>(stream)>>>(z, out, n, which);
+    return nst(cudaGetLastError());
+}
+
+swe_status swe_resample(const float *src, long long s_img, long long s_plane, long long s_pitch, int Ws, int Hs,
+                        float *dst, long long d_img, long long d_plane, long long d_pitch, int Wd, int Hd, int n,
+                        void *stream)
+{
+    if (!src || !dst || n < 1 || Wd < 1 || Hd < 1 || Wd > Ws || Hd > Hs || s_pitch < Ws || d_pitch < Wd)
+        return SWE_EINVAL;
+    resample_kernel<<<2368, 256, 0, static_cast<cudaStream_t>(stream)>>>(src, s_img, s_plane, s_pitch, Ws, Hs, dst,
+                                                                        d_img, d_plane, d_pitch, Wd, Hd, n);
     return nst(cudaGetLastError());
 }
 

@@ -90,6 +90,8 @@ _SIGS = {
                                 ctypes.POINTER(_d), _vp, _vp, _vp]),
     "swe_net_check": (_i, [_vp, _vp]),
     "swe_batch_learned_step": (_i, [_vp, _vp, _i, _i, _vp]),
+    "swe_net_set_loss_weighting": (_i, [_vp, ctypes.c_float, ctypes.c_float]),
+    "swe_resample": (_i, [_vp, _ll, _ll, _ll, _i, _i, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
     "swe_selftest_gelu": (_i, [_vp, _vp, _i, _i, _vp]),
     "swe_downsample": (_i, [_i, _vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
@@ -471,6 +473,9 @@ class Net:
         a = np.array([h0, sh, su, oh, ou], np.float32)
         check(lib().swe_net_set_norm(self.t, a.ctypes.data), "swe_net_set_norm")
 
+    def set_loss_weighting(self, power, floor=1.0):
+        check(lib().swe_net_set_loss_weighting(self.t, float(power), float(floor)), "swe_net_set_loss_weighting")
+
     def prep_input(self, n, state_ptr, img_stride, plane_stride, pitch, base_ptr=None, stream=None):
         check(lib().swe_net_prep_input(self.t, n, state_ptr, base_ptr, img_stride, plane_stride, pitch,
                                        stream if stream is not None else current_stream()), "swe_net_prep_input")
@@ -508,3 +513,8 @@ class Net:
 def swe_downsample(factor, fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc, n, stream=None):
     check(lib().swe_downsample(int(factor), fine, f_img, f_plane, f_pitch, coarse, c_img, c_plane, c_pitch, Wc, Hc,
                                n, stream if stream is not None else current_stream()), "swe_downsample")
+
+
+def swe_resample(src, s_img, s_plane, s_pitch, Ws, Hs, dst, d_img, d_plane, d_pitch, Wd, Hd, n, stream=None):
+    check(lib().swe_resample(src, s_img, s_plane, s_pitch, Ws, Hs, dst, d_img, d_plane, d_pitch, Wd, Hd, n,
+                             stream if stream is not None else current_stream()), "swe_resample")

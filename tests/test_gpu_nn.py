@@ -81,24 +81,27 @@ def test_forward_matches_oracle(n, H, W):
         assert cosine(got[i], ref[i]) >= 0.999
 
 
-def test_backward_matches_oracle():
+@pytest.mark.parametrize("power", [0.0, 1.0, 2.0])
+def test_backward_matches_oracle(power):
     import torch
     n, H, W = 2, 12, 260
     params = nn.init_params(5, out_scale=1.0)
     st = _state(n, H, W, 2)
     rng = np.random.default_rng(9)
-    target = rng.standard_normal((n, 3, H, W)).astype(np.float32)
+    target = (rng.standard_normal((n, 3, H, W)) * np.array([1.0, 6.0])[:, None, None, None]).astype(np.float32)
     dev = torch.from_numpy(st).cuda()
     tdev = torch.from_numpy(target).cuda()
     r_dev = torch.zeros((n, 3, H, W), dtype=torch.float32, device="cuda")
     from paper_1107_2157_gb300 import swe
     with _net_with(params, n, H, W) as net:
+        net.set_loss_weighting(power, 1.0)
         net.prep_input(n, dev.data_ptr(), 3 * H * W, H * W, W)  # state mode (no base)
         loss, g = net.train_step(n, tdev.data_ptr(), update=False, want_grads=True, resid_ptr=r_dev.data_ptr())
     op = _oracle_params(params)
     r, cache = nn.forward(op, _oracle_inputs(st))
-    ref_loss = nn.loss(r, target)
-    grads, _ = nn.backward(op, cache, r, target)
+    w = nn.image_weights(target, power, 1.0) if power else None
+    ref_loss = nn.loss(r, target, w)
+    grads, _ = nn.backward(op, cache, r, target, w)
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss
     assert rel_l2(r_dev.cpu().numpy(), r) <= 2e-2
     gg = swe.unflatten_params(g)
@@ -168,3 +171,19 @@ def test_device_erf_and_gelu_within_published_bound(which):
     else:
         ref = nn.gelu_grad(x)
         assert np.abs(got - ref).max() <= 2e-6
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024, 320, 384), (40, 30, 15, 12), (96, 96, 96, 32), (7, 9, 3, 4)])
+def test_area_resample_matches_oracle(shape):
+    import torch
+    from paper_1107_2157_gb300 import swe
+    Hs, Ws, Hd, Wd = shape
+    n = 2
+    rng = np.random.default_rng(21)
+    src = rng.standard_normal((n, 3, Hs, Ws)).astype(np.float32)
+    sd = torch.from_numpy(src).cuda()
+    dd = torch.zeros((n, 3, Hd, Wd), dtype=torch.float32, device="cuda")
+    swe.swe_resample(sd.data_ptr(), 3 * Hs * Ws, Hs * Ws, Ws, Ws, Hs, dd.data_ptr(), 3 * Hd * Wd, Hd * Wd, Wd, Wd, Hd, n)
+    torch.cuda.synchronize()
+    ref = nn.area_average(src.astype(np.float64), Hd, Wd)
+    assert np.abs(dd.cpu().numpy() - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())

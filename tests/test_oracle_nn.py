@@ -160,3 +160,57 @@ def test_learned_step_keeps_mass_under_projection():
     assert abs(oracle.mass(got[0], 1.0, 1.0) - m0) <= 1e-13 * m0
     free, _ = learned.corrected_step(s.h, s.hu, s.hv, 1.0, 1.0, 0.05, 9.8, p, norm, project_mass=False)
     assert abs(oracle.mass(free[0], 1.0, 1.0) - m0) > 1e-9 * m0  # the network alone does not
+
+
+def test_image_weights_closed_form():
+    t = np.stack([np.full((3, 4, 5), 0.5), np.full((3, 4, 5), 3.0), np.zeros((3, 4, 5))])
+    w = nn.image_weights(t, 2.0, 1.0)
+    assert np.allclose(w, [1.0, 1.0 / 9.0, 1.0], rtol=1e-15)     # floor 1 -> 0.25 counts as 1
+    w1 = nn.image_weights(t, 1.0, 0.01)
+    assert np.allclose(w1, [2.0, 1.0 / 3.0, 10.0], rtol=1e-15)
+    assert np.array_equal(nn.image_weights(t, 0.0, 1.0), np.ones(3))
+
+
+def test_weighted_backward_matches_central_differences():
+    rng = np.random.default_rng(13)
+    params = nn.init_params(8, hidden=6, out_scale=1.0)
+    x0 = rng.standard_normal((3, 3, 7, 6))
+    t = rng.standard_normal((3, 3, 7, 6)) * np.array([0.5, 2.0, 10.0])[:, None, None, None]
+    w = nn.image_weights(t, 1.0, 1.0)
+    r, cache = nn.forward(params, x0)
+    grads, _ = nn.backward(params, cache, r, t, w)
+    for name in ("W1", "b2", "W3"):
+        p = params[name]
+        for ix in [tuple(rng.integers(0, s) for s in p.shape) for _ in range(4)]:
+            old = p[ix]
+            h = 1e-5
+            p[ix] = old + h
+            lp = nn.loss(nn.forward(params, x0)[0], t, w)
+            p[ix] = old - h
+            lm = nn.loss(nn.forward(params, x0)[0], t, w)
+            p[ix] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - grads[name][ix]) <= 1e-6 * max(abs(fd), 1e-3), (name, ix)
+
+
+def test_area_average_pins():
+    """Worked 1D case, integer ratios = block average, constants and
+    integrals kept, and a brute-force subdivision for fractional ratios."""
+    u = np.arange(5, dtype=np.float64)[None, :]                # 5 -> 2 cells, f = 2.5
+    d = nn.area_average(u, 1, 2)
+    assert np.allclose(d, [[(0 + 1 + 0.5 * 2) / 2.5, (0.5 * 2 + 3 + 4) / 2.5]], rtol=0, atol=1e-15)
+    rng = np.random.default_rng(17)
+    v = rng.standard_normal((2, 3, 12, 18))
+    assert np.allclose(nn.area_average(v, 4, 6), nn.block_average(v, 3), atol=1e-14)
+    for (hs, ws, hd, wd) in [(16, 20, 5, 6), (1024, 1024, 320, 384), (9, 7, 9, 3), (768, 768, 256, 256)]:
+        w = rng.standard_normal((hs, ws))
+        a = nn.area_average(w, hd, wd)
+        assert abs(a.sum() * (hs / hd) * (ws / wd) - w.sum()) <= 1e-9 * np.abs(w).sum()
+        assert np.allclose(nn.area_average(np.full((hs, ws), 1.7), hd, wd), 1.7, atol=1e-13)
+    # brute force: split every source cell into 10 x 10 equal parts (the
+    # same piecewise-constant field); ratios 2.5 and 3.2 then become the
+    # integer block sizes 25 and 32 of a plain block average
+    w = rng.standard_normal((10, 16))
+    fine = np.repeat(np.repeat(w, 10, axis=0), 10, axis=1)     # 100 x 160
+    ref = fine.reshape(4, 25, 5, 32).mean(axis=(1, 3))
+    assert np.allclose(nn.area_average(w, 4, 5), ref, atol=1e-13)
