@@ -35,19 +35,67 @@ __device__ __forceinline__ float erf_as(float x, float &gauss)
 // divided by 2^(-1/4) -- coefficients c_k = a_k / (2^(-1/4) sqrt(2)^k),
 // c_0 = 2^(1/4) -- the fourth power of its reciprocal is
 // q = (1 - erf(x)) / 2, so GELU = z (1 - q) for z >= 0 and z q for z < 0:
-// one reciprocal and nine other operations.  The GELU error is at most
-// 6.9e-4 (2.3e-4 |z| for |z| > 1), about one bf16 half-ulp of the output.
+// written without a branch as GELU = z/2 + |z| (1/2 - q): one reciprocal
+// and eight other operations.  The GELU error is at most 6.9e-4
+// (2.3e-4 |z| for |z| > 1), about one bf16 half-ulp of the output.
+constexpr float kGeluC4 = 2.322164733e-02f, kGeluC3 = 4.086756578e-04f, kGeluC2 = 1.369901190e-01f,
+                kGeluC1 = 2.340996757e-01f, kGeluC0 = 1.189207115e+00f;
+
 __device__ __forceinline__ float gelu_f(float z)
 {
     const float u = fabsf(z);
-    float d = fmaf(2.322164733e-02f, u, 4.086756578e-04f);
-    d = fmaf(d, u, 1.369901190e-01f);
-    d = fmaf(d, u, 2.340996757e-01f);
-    d = fmaf(d, u, 1.189207115e+00f);
+    float d = fmaf(kGeluC4, u, kGeluC3);
+    d = fmaf(d, u, kGeluC2);
+    d = fmaf(d, u, kGeluC1);
+    d = fmaf(d, u, kGeluC0);
     const float r = rcp(d);
-    const float r2 = r * r;
-    const float q = r2 * r2;
-    return z * (z >= 0.0f ? 1.0f - q : q);
+    const float r2 = __fmul_rn(r, r);
+    const float q = __fmul_rn(r2, r2);
+    return fmaf(u, fmaf(q, -1.0f, 0.5f), __fmul_rn(0.5f, z));
+}
+
+// Packed pairs of FP32 values (the sm_100-family f32x2 instructions: two
+// lanes of the same IEEE operation in one instruction).
+__device__ __forceinline__ unsigned long long f32x2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f32x2_split(unsigned long long v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma_x2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul_x2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// gelu_f of two values, the polynomial and products done pairwise; the
+// same operations in the same order, so the same bits as gelu_f.
+__device__ __forceinline__ void gelu_f2(float z0, float z1, float &g0, float &g1)
+{
+    const unsigned long long u = f32x2(fabsf(z0), fabsf(z1));
+    unsigned long long d = fma_x2(f32x2(kGeluC4, kGeluC4), u, f32x2(kGeluC3, kGeluC3));
+    d = fma_x2(d, u, f32x2(kGeluC2, kGeluC2));
+    d = fma_x2(d, u, f32x2(kGeluC1, kGeluC1));
+    d = fma_x2(d, u, f32x2(kGeluC0, kGeluC0));
+    float d0, d1;
+    f32x2_split(d, d0, d1);
+    const unsigned long long r = f32x2(rcp(d0), rcp(d1));
+    const unsigned long long r2 = mul_x2(r, r);
+    const unsigned long long q = mul_x2(r2, r2);
+    const unsigned long long hz = mul_x2(f32x2(0.5f, 0.5f), f32x2(z0, z1));
+    const unsigned long long g = fma_x2(u, fma_x2(q, f32x2(-1.0f, -1.0f), f32x2(0.5f, 0.5f)), hz);
+    f32x2_split(g, g0, g1);
 }
 
 // Derivative 0.5 (1 + erf(z / sqrt 2)) + z phi(z) for the backward pass,

@@ -192,11 +192,11 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bia
     arm<CPT>(taddr, bias);
 #pragma unroll
     for (int c = 0; c < CPT / 8; ++c) {
-        const float y0 = gelu_f(v[8 * c + 0]), y1 = gelu_f(v[8 * c + 1]);
-        const float y2 = gelu_f(v[8 * c + 2]), y3 = gelu_f(v[8 * c + 3]);
-        const float y4 = gelu_f(v[8 * c + 4]), y5 = gelu_f(v[8 * c + 5]);
-        const float y6 = gelu_f(v[8 * c + 6]), y7 = gelu_f(v[8 * c + 7]);
-        const uint4 o = make_uint4(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3), pack_bf16x2(y4, y5), pack_bf16x2(y6, y7));
+        float y[8];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) gelu_f2(v[8 * c + k], v[8 * c + k + 1], y[k], y[k + 1]);
+        const uint4 o = make_uint4(pack_bf16x2(y[0], y[1]), pack_bf16x2(y[2], y[3]), pack_bf16x2(y[4], y[5]),
+                                   pack_bf16x2(y[6], y[7]));
         *reinterpret_cast<uint4 *>(dst + c * strip) = valid ? o : zero4();
     }
 }
