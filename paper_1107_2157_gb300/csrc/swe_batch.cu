@@ -122,10 +122,80 @@ __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *_
 }
 
 // ---------------------------------------------------------------------------
+// The same with temporal blocking: two steps per pass over the tile list.
+// Each tile is staged with a two-cell y-halo (one TMA box of TY + 4 rows per
+// field) and advanced twice by tb2_tile_compute into the other buffer; a
+// grid barrier separates the passes.  An odd last step takes one step from
+// the same box (tile row 0 at box row 2).  Same bits as the one-step
+// kernels; DRAM sees each cell once per two steps (plus the halo rows).
+// ---------------------------------------------------------------------------
+template <int NWARP, int RY>
+__global__ void __launch_bounds__(NWARP * 32) batch_tb2_kernel(const BatchInst *__restrict__ inst,
+                                                               const CUtensorMap *__restrict__ maps,
+                                                               const TileRec *__restrict__ tiles, int ntiles,
+                                                               int n_steps, int parity0, GridBarrier *gbar, int *err,
+                                                               int *flags)
+{
+    using B = Tb2Cfg<float, NWARP, RY>;
+    using C = typename B::C;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *iH = reinterpret_cast<float *>(smem);
+    float *iU = reinterpret_cast<float *>(smem + B::IN_STRIDE);
+    float *iV = reinterpret_cast<float *>(smem + 2 * B::IN_STRIDE);
+    float *mH_ = reinterpret_cast<float *>(smem + 3 * B::IN_STRIDE);
+    float *mU_ = reinterpret_cast<float *>(smem + 3 * B::IN_STRIDE + C::BOX_STRIDE);
+    float *mV_ = reinterpret_cast<float *>(smem + 3 * B::IN_STRIDE + 2 * C::BOX_STRIDE);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 3 * B::IN_STRIDE + 3 * C::BOX_STRIDE);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int cur = parity0;
+    const int pairs = n_steps / 2, passes = pairs + (n_steps & 1);
+    for (int p = 0; p < passes; ++p, cur ^= 1) {
+        const bool two = p < pairs;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const TileRec r = tiles[t];
+            const int x0 = (int)r.bx * C::TX, y0 = (int)r.by * C::TY;
+            __syncthreads();  // the previous tile is done with the boxes
+            if (threadIdx.x == 0) {
+                const CUtensorMap *m = maps + ((size_t)r.inst * 2 + cur) * 3;
+                fence_proxy_async_global();  // other CTAs' stores of the last pass -> TMA reads
+                mbar_arrive_expect_tx(bar, (uint32_t)(3 * B::IN_BYTES));
+                tma_load_2d(iH, m + 0, bar, x0 - C::AX, y0 - 2);
+                tma_load_2d(iU, m + 1, bar, x0 - C::AX, y0 - 2);
+                tma_load_2d(iV, m + 2, bar, x0 - C::AX, y0 - 2);
+            }
+            if (!__syncthreads_and(mbar_wait_bounded(bar, phase, err))) return;
+            phase ^= 1u;
+            const BatchInst *I = inst + r.inst;
+            float *o = I->buf[cur ^ 1];
+            const long long plane = I->plane, pitch = I->pitch;
+            const int nx = I->nx, ny = I->ny;
+            const Coef<float> k = I->k;
+            bool bad;
+            if (two)
+                bad = tb2_tile_compute<float, NWARP, RY>(iH, iU, iV, mH_, mU_, mV_, o, o + plane, o + 2 * plane, nx,
+                                                          ny, pitch, x0, y0, k);
+            else if (x0 == 0 || x0 + C::TX >= nx)
+                bad = tiled_compute<float, NWARP, RY, true, 2>(iH, iU, iV, o, o + plane, o + 2 * plane, nx, ny, pitch,
+                                                               x0, y0, k);
+            else
+                bad = tiled_compute<float, NWARP, RY, false, 2>(iH, iU, iV, o, o + plane, o + 2 * plane, nx, ny,
+                                                                pitch, x0, y0, k);
+            if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags[r.inst], SWE_FLAG_NONPOSITIVE);
+        }
+        if (!grid_sync_bounded(gbar, gridDim.x, err)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Variants the autotuner chooses from
 // ---------------------------------------------------------------------------
 struct Variant {
-    int nwarp, ry, stages;
+    int nwarp, ry, stages, depth;
     int tile_x, tile_y, box_w, box_h;
     size_t smem;
     const void *func;
@@ -136,9 +206,21 @@ static Variant make_variant()
 {
     using B = BatchCfg<NWARP, RY, STAGES>;
     using C = typename B::C;
-    return Variant{NWARP, RY, STAGES, C::TX, C::TY, C::BW, C::BH, B::SMEM,
+    return Variant{NWARP, RY, STAGES, 1, C::TX, C::TY, C::BW, C::BH, B::SMEM,
                    reinterpret_cast<const void *>(&batch_lw_kernel<NWARP, RY, STAGES>)};
 }
+
+template <int NWARP, int RY>
+static Variant make_variant_tb2()
+{
+    using B = Tb2Cfg<float, NWARP, RY>;
+    using C = typename B::C;
+    return Variant{NWARP, RY, 1, 2, C::TX, C::TY, C::BW, B::BH_IN, B::SMEM,
+                   reinterpret_cast<const void *>(&batch_tb2_kernel<NWARP, RY>)};
+}
+
+// Buffer swaps (= launches of a step pass) that n steps take with a variant.
+static int swaps_of(const Variant &V, int n) { return V.depth == 2 ? n / 2 + (n & 1) : n; }
 
 static const std::vector<Variant> &variants()
 {
@@ -148,6 +230,9 @@ static const std::vector<Variant> &variants()
         make_variant<4, 8, 1>(),   // 128x32 tiles, single stage
         make_variant<8, 4, 2>(),   // 128x32 tiles, 8 warps, double-buffered
         make_variant<4, 16, 1>(),  // 128x64 tiles, single stage
+        make_variant_tb2<8, 4>(),  // two steps per pass: 128x32 tiles, 8 warps
+        make_variant_tb2<4, 4>(),  // two steps per pass: 128x16 tiles
+        make_variant_tb2<8, 2>(),  // two steps per pass: 128x16 tiles, 8 warps
     };
     return v;
 }
@@ -384,13 +469,13 @@ static swe_status run_steps(swe_batch *b, int n_steps, cudaStream_t s)
         }
         if (b->graph_ok) {
             B_TRY(cudaGraphLaunch(it->second, s));
-            b->cur ^= (n_steps & 1);
+            b->cur ^= (swaps_of(variants()[b->variant], n_steps) & 1);
             b->launches += 1;
             return SWE_OK;
         }
     }
     B_TRY(launch_direct(b, n_steps, parity0, s));
-    b->cur ^= (n_steps & 1);
+    b->cur ^= (swaps_of(variants()[b->variant], n_steps) & 1);
     b->launches += 1;
     return SWE_OK;
 }
@@ -433,16 +518,30 @@ static bool cache_lookup(const char *path, const std::string &key, int *v, int *
     return found;
 }
 
-static void cache_store(const char *path, const std::string &key, int v, int cps, double ms)
+struct Trial {
+    int v, cps;
+    double ms;
+};
+
+// Appends the tuner's decision for ``key``: first a line with every trial
+// (variant, CTAs per SM, depth, ms per step), then the winner's line, the
+// one cache_lookup reads.
+static void cache_store(const char *path, const std::string &key, int v, int cps, double ms,
+                        const std::vector<Trial> &trials)
 {
     if (!path || !*path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
+    std::fprintf(f, "{\"key\": \"%s\", \"trials\": [", key.c_str());
+    for (size_t i = 0; i < trials.size(); ++i)
+        std::fprintf(f, "%s{\"v\": %d, \"cps\": %d, \"depth\": %d, \"ms\": %.6f}", i ? ", " : "", trials[i].v,
+                     trials[i].cps, variants()[trials[i].v].depth, trials[i].ms);
+    std::fprintf(f, "]}\n");
     const Variant &V = variants()[v];
     std::fprintf(f,
                  "{\"key\": \"%s\", \"variant\": %d, \"ctas_per_sm\": %d, \"tile_x\": %d, \"tile_y\": %d, "
-                 "\"stages\": %d, \"depth\": 1, \"ms_per_step\": %.6f}\n",
-                 key.c_str(), v, cps, V.tile_x, V.tile_y, V.stages, ms);
+                 "\"stages\": %d, \"depth\": %d, \"ms_per_step\": %.6f}\n",
+                 key.c_str(), v, cps, V.tile_x, V.tile_y, V.stages, V.depth, ms);
     std::fclose(f);
 }
 
@@ -672,6 +771,7 @@ swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream)
     cudaEventCreate(&e1);
     double best_ms = 1e30;
     int best_v = 0, best_c = 1;
+    std::vector<Trial> trials;
     const int trial_steps = 8;
     swe_status st = SWE_OK;
     for (int vi = 0; vi < (int)variants().size() && st == SWE_OK; ++vi) {
@@ -690,6 +790,7 @@ swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream)
                 best = std::min(best, ms);
             }
             const double per = best / trial_steps;
+            trials.push_back(Trial{vi, c, per});
             if (per < best_ms) {
                 best_ms = per;
                 best_v = vi;
@@ -708,7 +809,7 @@ swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream)
     st = configure(b, best_v, best_c);
     if (st == SWE_OK) {
         b->tuned = 1;
-        cache_store(path, key, best_v, best_c, best_ms);
+        cache_store(path, key, best_v, best_c, best_ms, trials);
     }
     return st;
 }
@@ -725,7 +826,7 @@ swe_status swe_batch_query(swe_batch *b, int key, long long *value)
         case SWE_BQ_TILE_X: *value = V.tile_x; break;
         case SWE_BQ_TILE_Y: *value = V.tile_y; break;
         case SWE_BQ_STAGES: *value = V.stages; break;
-        case SWE_BQ_DEPTH: *value = 1; break;
+        case SWE_BQ_DEPTH: *value = V.depth; break;
         case SWE_BQ_GRAPH: *value = b->graph_ok ? 1 : 0; break;
         case SWE_BQ_LAUNCHES: *value = b->launches; break;
         case SWE_BQ_TUNED: *value = b->tuned; break;

@@ -22,24 +22,10 @@ static Coef<T> make_coef(double dx, double dy, double dt, double g)
 }
 
 // ---------------------------------------------------------------------------
-// Two steps per launch (temporal blocking).  The CTA stages its tile with a
-// two-cell halo (box origin (x0 - AX, y0 - 2)), computes the intermediate
-// state on the tile plus a one-cell ring into a second shared-memory box
-// laid out like the one-step kernel's input box, and then runs the one-step
-// tile routine on it.  Every cell goes through the same face and update
-// functions as in the one-step kernel, so two steps here equal two one-step
-// launches bit for bit, while DRAM sees each cell read and written once per
-// two steps.
+// Two steps per launch (temporal blocking): one CTA per tile stages the
+// tile with a two-cell halo and runs tb2_tile_compute (swe_tile.cuh); DRAM
+// sees each cell read and written once per two steps.
 // ---------------------------------------------------------------------------
-template <typename T, int NWARP, int RY>
-struct Tb2Cfg {
-    using C = TiledCfg<T, NWARP, RY>;
-    static constexpr int BH_IN = C::TY + 4;
-    static constexpr size_t IN_BYTES = (size_t)C::BW * BH_IN * sizeof(T);
-    static constexpr size_t IN_STRIDE = (IN_BYTES + 127) / 128 * 128;
-    static constexpr size_t SMEM = 3 * IN_STRIDE + 3 * C::BOX_STRIDE + 128;
-};
-
 template <typename T, int NWARP, int RY>
 __global__ void __launch_bounds__(NWARP * 32) lw_tb2_kernel(const __grid_constant__ CUtensorMap mH,
                                                             const __grid_constant__ CUtensorMap mU,
@@ -50,7 +36,6 @@ __global__ void __launch_bounds__(NWARP * 32) lw_tb2_kernel(const __grid_constan
 {
     using B = Tb2Cfg<T, NWARP, RY>;
     using C = typename B::C;
-    constexpr int VX = C::VX;
     extern __shared__ __align__(128) unsigned char smem[];
     T *iH = reinterpret_cast<T *>(smem);
     T *iU = reinterpret_cast<T *>(smem + B::IN_STRIDE);
@@ -70,49 +55,8 @@ __global__ void __launch_bounds__(NWARP * 32) lw_tb2_kernel(const __grid_constan
         tma_load_2d(iV, &mV, bar, x0 - C::AX, y0 - 2);
     }
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0, err)) return;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cx = lane * VX, gx = x0 + cx, rb = warp * RY;
-    const bool xedge = (x0 == 0) || (x0 + C::TX >= nx);
-
-    // phase 1: intermediate state on rows [-1, TY] of the tile's columns; the
-    // first and last warp also take the ring rows -1 and TY
-    {
-        int r0 = warp == 0 ? -1 : rb;
-        int r1 = warp == NWARP - 1 ? rb + RY + 1 : rb + RY;
-        r0 = max(r0, -y0);
-        r1 = min(r1, ny - y0);
-        auto to_mid = [&](int r, const T(&h)[VX], const T(&u)[VX], const T(&v)[VX]) {
-            const int o = (r + 1) * C::BW + cx + C::AX;
-            store_vec<T, VX>(mH_ + o, h);
-            store_vec<T, VX>(mU_ + o, u);
-            store_vec<T, VX>(mV_ + o, v);
-        };
-        if (xedge)
-            strip_compute<T, VX, true>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
-        else
-            strip_compute<T, VX, false>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
-        // the ring columns -1 and TX, one cell at a time
-        for (int idx = threadIdx.x; idx < 2 * (C::TY + 2); idx += blockDim.x) {
-            const int c = (idx & 1) ? C::TX : -1;
-            const int r = (idx >> 1) - 1;
-            const int cgx = x0 + c, gy = y0 + r;
-            if (cgx < 0 || cgx >= nx || gy < 0 || gy >= ny) continue;
-            T h, hu, hv;
-            box_cell<T>(iH, iU, iV, C::BW, C::AX, 2, c, r, cgx, gy, nx, ny, k, h, hu, hv);
-            const int o = (r + 1) * C::BW + c + C::AX;
-            mH_[o] = h;
-            mU_[o] = hu;
-            mV_[o] = hv;
-        }
-    }
-    __syncthreads();
-    // phase 2: the second step from the intermediate box to global memory
-    if (xedge)
-        tiled_compute<T, NWARP, RY, true>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
-    else
-        tiled_compute<T, NWARP, RY, false>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
+    if (!__syncthreads_and(mbar_wait_bounded(bar, 0, err))) return;
+    tb2_tile_compute<T, NWARP, RY>(iH, iU, iV, mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
 }
 
 // Two-step kernel shapes (warps x rows per warp): 0: 4x8 (tile 128x32,

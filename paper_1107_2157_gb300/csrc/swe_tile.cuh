@@ -156,9 +156,10 @@ __device__ __forceinline__ void box_cell(const T *sH, const T *sU, const T *sV, 
     lw_update(h, hu, hv, Fl, Fr, Gd, Gu, k);
 }
 
-// Computes one output tile from the staged box (see TiledCfg) and stores it.
-// Returns true if some stored depth is not positive (h <= 0 or NaN).
-template <typename T, int NWARP, int RY, bool XEDGE>
+// Computes one output tile from the staged box (see TiledCfg; the box's
+// first row is tile row -ROW_OFF) and stores it.  Returns true if some
+// stored depth is not positive (h <= 0 or NaN).
+template <typename T, int NWARP, int RY, bool XEDGE, int ROW_OFF = 1>
 __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T *sV, T *__restrict__ oH,
                                               T *__restrict__ oU, T *__restrict__ oV, int nx, int ny,
                                               long long pitch, int x0, int y0, const Coef<T> &k)
@@ -172,7 +173,7 @@ __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T 
     const int rb = warp * RY;
     const int re = min(rb + RY, ny - y0);
     bool bad = false;
-    strip_compute<T, VX, XEDGE>(sH, sU, sV, C::BW, C::AX, 1, rb, re, cx, gx, nx, ny, y0, k,
+    strip_compute<T, VX, XEDGE>(sH, sU, sV, C::BW, C::AX, ROW_OFF, rb, re, cx, gx, nx, ny, y0, k,
                                 [&](int r, const T(&oh)[VX], const T(&ou)[VX], const T(&ov)[VX]) {
                                     if (gx < nx) {
 #pragma unroll
@@ -185,6 +186,72 @@ __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T 
                                     }
                                 });
     return bad;
+}
+
+// ---------------------------------------------------------------------------
+// Two steps of one tile (temporal blocking).  The input box holds the tile
+// with a two-cell y-halo (box origin (x0 - AX, y0 - 2), TY + 4 rows); the
+// intermediate state of the tile plus a one-cell ring goes to a second box
+// laid out like the one-step kernel's input box, and the one-step tile
+// routine takes the second step from there.  Every cell goes through the
+// same face and update functions as in the one-step kernel, so the result
+// equals two one-step passes bit for bit.  All threads of the CTA call it.
+// ---------------------------------------------------------------------------
+template <typename T, int NWARP, int RY>
+struct Tb2Cfg {
+    using C = TiledCfg<T, NWARP, RY>;
+    static constexpr int BH_IN = C::TY + 4;
+    static constexpr size_t IN_BYTES = (size_t)C::BW * BH_IN * sizeof(T);
+    static constexpr size_t IN_STRIDE = (IN_BYTES + 127) / 128 * 128;
+    static constexpr size_t SMEM = 3 * IN_STRIDE + 3 * C::BOX_STRIDE + 128;
+};
+
+template <typename T, int NWARP, int RY>
+__device__ __forceinline__ bool tb2_tile_compute(const T *iH, const T *iU, const T *iV, T *mH_, T *mU_, T *mV_,
+                                                 T *__restrict__ oH, T *__restrict__ oU, T *__restrict__ oV,
+                                                 int nx, int ny, long long pitch, int x0, int y0, const Coef<T> &k)
+{
+    using C = TiledCfg<T, NWARP, RY>;
+    constexpr int VX = C::VX;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cx = lane * VX, gx = x0 + cx, rb = warp * RY;
+    const bool xedge = (x0 == 0) || (x0 + C::TX >= nx);
+
+    // phase 1: intermediate state on rows [-1, TY] of the tile's columns; the
+    // first and last warp also take the ring rows -1 and TY
+    {
+        int r0 = warp == 0 ? -1 : rb;
+        int r1 = warp == NWARP - 1 ? rb + RY + 1 : rb + RY;
+        r0 = max(r0, -y0);
+        r1 = min(r1, ny - y0);
+        auto to_mid = [&](int r, const T(&h)[VX], const T(&u)[VX], const T(&v)[VX]) {
+            const int o = (r + 1) * C::BW + cx + C::AX;
+            store_vec<T, VX>(mH_ + o, h);
+            store_vec<T, VX>(mU_ + o, u);
+            store_vec<T, VX>(mV_ + o, v);
+        };
+        if (xedge)
+            strip_compute<T, VX, true>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
+        else
+            strip_compute<T, VX, false>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
+        // the ring columns -1 and TX, one cell at a time
+        for (int idx = threadIdx.x; idx < 2 * (C::TY + 2); idx += blockDim.x) {
+            const int c = (idx & 1) ? C::TX : -1;
+            const int r = (idx >> 1) - 1;
+            const int cgx = x0 + c, gy = y0 + r;
+            if (cgx < 0 || cgx >= nx || gy < 0 || gy >= ny) continue;
+            T h, hu, hv;
+            box_cell<T>(iH, iU, iV, C::BW, C::AX, 2, c, r, cgx, gy, nx, ny, k, h, hu, hv);
+            const int o = (r + 1) * C::BW + c + C::AX;
+            mH_[o] = h;
+            mU_[o] = hu;
+            mV_[o] = hv;
+        }
+    }
+    __syncthreads();
+    // phase 2: the second step from the intermediate box to global memory
+    if (xedge) return tiled_compute<T, NWARP, RY, true>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
+    return tiled_compute<T, NWARP, RY, false>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
 }
 
 }  // namespace swe

@@ -117,6 +117,7 @@ def test_tuner_picks_a_variant_and_caches_it(tmp_path):
     dts = _dts(states, dxs, dys)
     cache = str(tmp_path / "tune.jsonl")
     with _make_batch(sizes, states, dxs, dys, dts) as b:
+        nvar = b.query(swe.SWE_BQ_VARIANT_COUNT)
         before = [b.get_state(i) for i in range(len(sizes))]
         b.tune(cache)
         assert b.query(swe.SWE_BQ_TUNED) == 1
@@ -125,11 +126,20 @@ def test_tuner_picks_a_variant_and_caches_it(tmp_path):
             after = b.get_state(i)
             assert all(np.array_equal(a, c) for a, c in zip(after, before[i]))
     lines = [json.loads(x) for x in open(cache)]
-    assert len(lines) == 1 and lines[0]["ctas_per_sm"] >= 1
+    winners = [ln for ln in lines if "variant" in ln]
+    trials = [ln for ln in lines if "trials" in ln]
+    assert len(winners) == 1 and winners[0]["ctas_per_sm"] >= 1
+    # every variant (both temporal-blocking depths) was timed
+    assert len(trials) == 1
+    assert {t["v"] for t in trials[0]["trials"]} == set(range(nvar))
+    assert {t["depth"] for t in trials[0]["trials"]} == {1, 2}
+    best = min(trials[0]["trials"], key=lambda t: t["ms"])
+    assert (best["v"], best["cps"]) == (winners[0]["variant"], winners[0]["ctas_per_sm"])
     with _make_batch(sizes, states, dxs, dys, dts) as b2:
         b2.tune(cache)
         assert b2.query(swe.SWE_BQ_TUNED) == 2
-        assert b2.query(swe.SWE_BQ_VARIANT) == lines[0]["variant"]
+        assert b2.query(swe.SWE_BQ_VARIANT) == winners[0]["variant"]
+        assert b2.query(swe.SWE_BQ_DEPTH) == best["depth"]
 
 
 @pytest.mark.parametrize("which", [0, 1])
