@@ -56,8 +56,14 @@ typedef enum {
     SWE_KERNEL_AUTO = 0,   /* the fastest variant for the dtype and size */
     SWE_KERNEL_NAIVE = 1,  /* one thread per cell, neighbours from global memory */
     SWE_KERNEL_TILED = 2,  /* TMA tile + halo in shared memory, one step per launch */
-    SWE_KERNEL_TEMPORAL = 3 /* TMA tile + 2-cell halo, 2 steps per launch (an odd
+    SWE_KERNEL_TEMPORAL = 3, /* TMA tile + 2-cell halo, 2 steps per launch (an odd
                                last step uses the one-step kernel); same bits */
+    SWE_KERNEL_PACKED = 4    /* FP32 only: the state packed as (h, hu, hv, 0) 16-byte
+                               cells on the device (Sec. 5's packed vector type) instead
+                               of three planes; TMA tile + halo, one step per launch;
+                               32 B of HBM traffic per cell-update (planes: 24); same
+                               bits as the plane kernels.  State transfers and the
+                               reductions go through plane copies. */
 } swe_kernel;
 
 typedef struct {
@@ -140,7 +146,7 @@ typedef enum {
     SWE_Q_LAUNCHES = 3,         /* step-kernel launches enqueued so far */
     SWE_Q_TILE_X = 4,           /* tile width in cells */
     SWE_Q_TILE_Y = 5,           /* tile height in cells */
-    SWE_Q_STATE_PTR = 6,        /* device address of the current H plane */
+    SWE_Q_STATE_PTR = 6,        /* device address of the current H plane (SWE_KERNEL_PACKED: of the packed state) */
     SWE_Q_STEPS_PER_LAUNCH = 7  /* steps a full step-kernel launch advances */
 } swe_query_key;
 

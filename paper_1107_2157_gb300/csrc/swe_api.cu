@@ -25,6 +25,13 @@ struct swe_ctx {
     int tb_variant = 0;         // two-step kernel shape
     CUtensorMap maps[2][3];     // TMA maps of both buffers, one-step box
     CUtensorMap maps_tb[2][3];  // TMA maps of both buffers, two-step box
+    // SWE_KERNEL_PACKED: the state lives in packed[cur] ((h, hu, hv, 0) cells,
+    // ppitch per row); the planes are a staging copy, stale after steps until
+    // a transfer or a reduction unpacks them.
+    void *packed[2] = {nullptr, nullptr};
+    long long ppitch = 0;
+    CUtensorMap maps_pk[2];
+    bool planes_stale = false;
     double *scratch = nullptr;  // reduction partials (device)
     double *result = nullptr;   // reduction results (device, 4 doubles)
     double *host_result = nullptr;  // pinned copy of result
@@ -58,6 +65,24 @@ bool encode_plane_map(CUtensorMap *map, int dtype, const void *base, int nx, int
                                 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_packed_map(CUtensorMap *map, const void *base, int nx, int ny, long long ppitch, int box_x, int box_y)
+{
+    if (!g_encode) {
+        CUtensorMap dummy;
+        float one = 0.0f;
+        (void)encode_plane_map(&dummy, SWE_F32, &one, 1, 1, 32, 4, 1);  // resolves the entry point
+    }
+    if (!g_encode) return false;
+    const cuuint64_t dims[3] = {4, (cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t strides[2] = {16, (cuuint64_t)ppitch * 16};
+    const cuuint32_t box[3] = {4, (cuuint32_t)box_x, (cuuint32_t)box_y};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -135,6 +160,8 @@ void swe_destroy(swe_ctx *c)
     cudaDeviceSynchronize();
     cudaFree(c->state[0]);
     cudaFree(c->state[1]);
+    cudaFree(c->packed[0]);
+    cudaFree(c->packed[1]);
     cudaFree(c->scratch);
     cudaFree(c->result);
     cudaFree(c->err);
@@ -153,7 +180,8 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536) return SWE_EINVAL;
     if (!finite_pos(dx) || !finite_pos(dy) || !finite_pos(dt) || !finite_pos(g)) return SWE_EINVAL;
     if (o.dtype != SWE_F32 && o.dtype != SWE_F64) return SWE_EINVAL;
-    if (o.kernel < SWE_KERNEL_AUTO || o.kernel > SWE_KERNEL_TEMPORAL) return SWE_EINVAL;
+    if (o.kernel < SWE_KERNEL_AUTO || o.kernel > SWE_KERNEL_PACKED) return SWE_EINVAL;
+    if (o.kernel == SWE_KERNEL_PACKED && o.dtype != SWE_F32) return SWE_EUNSUPPORTED;
     if (o.depth < 0 || o.depth > 2) return SWE_EUNSUPPORTED;
 
     swe_ctx *c = new (std::nothrow) swe_ctx();
@@ -191,6 +219,17 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     if ((st = cuda_status(cudaMemset(c->err, 0, sizeof(int)))) != SWE_OK) return fail(st);
     if ((st = cuda_status(cudaMallocHost(&c->host_result, 4 * sizeof(double)))) != SWE_OK) return fail(st);
 
+    if (c->kernel == SWE_KERNEL_PACKED) {
+        c->ppitch = ((long long)nx + 7) / 8 * 8;  // 128-byte rows
+        const size_t pbytes = (size_t)c->ppitch * ny * 16;
+        int bw, bh;
+        packed_box(&bw, &bh);
+        for (int b = 0; b < 2; ++b) {
+            if ((st = cuda_status(cudaMalloc(&c->packed[b], pbytes))) != SWE_OK) return fail(st);
+            if ((st = cuda_status(cudaMemset(c->packed[b], 0, pbytes))) != SWE_OK) return fail(st);
+            if (!encode_packed_map(&c->maps_pk[b], c->packed[b], nx, ny, c->ppitch, bw, bh)) return fail(SWE_ECUDA);
+        }
+    }
     if (c->kernel == SWE_KERNEL_TILED || c->kernel == SWE_KERNEL_TEMPORAL) {
         int bw, bh, tw, th;
         tiled_box(c->dtype, &bw, &bh);
@@ -219,9 +258,20 @@ swe_status swe_set_dt(swe_ctx *c, double dt)
     return SWE_OK;
 }
 
+// Packed contexts: brings the plane copy of the current state up to date.
+static cudaError_t sync_planes(swe_ctx *c, cudaStream_t s)
+{
+    if (c->kernel != SWE_KERNEL_PACKED || !c->planes_stale) return cudaSuccess;
+    const cudaError_t e = launch_pack(plane_ptr(c, c->cur, 0), plane_ptr(c, c->cur, 1), plane_ptr(c, c->cur, 2),
+                                      c->pitch, c->packed[c->cur], c->ppitch, c->nx, c->ny, true, s);
+    if (e == cudaSuccess) c->planes_stale = false;
+    return e;
+}
+
 static swe_status copy_planes(swe_ctx *c, void *const *user, long long ld, bool to_device, cudaStream_t s)
 {
     if (ld < c->nx) return SWE_EINVAL;
+    if (!to_device) SWE_TRY(sync_planes(c, s));
     for (int k = 0; k < 3; ++k)
         if (!user[k]) return SWE_EINVAL;
     for (int k = 0; k < 3; ++k) {
@@ -233,6 +283,11 @@ static swe_status copy_planes(swe_ctx *c, void *const *user, long long ld, bool 
         else
             SWE_TRY(cudaMemcpy2DAsync(user[k], (size_t)ld * c->esize, dev, (size_t)c->pitch * c->esize, w, c->ny,
                                       cudaMemcpyDefault, s));
+    }
+    if (to_device && c->kernel == SWE_KERNEL_PACKED) {
+        SWE_TRY(launch_pack(plane_ptr(c, c->cur, 0), plane_ptr(c, c->cur, 1), plane_ptr(c, c->cur, 2), c->pitch,
+                            c->packed[c->cur], c->ppitch, c->nx, c->ny, false, s));
+        c->planes_stale = false;
     }
     return SWE_OK;
 }
@@ -272,7 +327,11 @@ swe_status swe_step(swe_ctx *c, int n_steps, void *stream)
     for (; n < n_steps; ++n) {
         const int in = c->cur, outb = c->cur ^ 1;
         cudaError_t e;
-        if (c->kernel == SWE_KERNEL_NAIVE)
+        if (c->kernel == SWE_KERNEL_PACKED) {
+            e = launch_packed(&c->maps_pk[in], c->packed[outb], c->nx, c->ny, c->ppitch, c->dx, c->dy, c->dt, c->g,
+                              c->err, s);
+            c->planes_stale = true;
+        } else if (c->kernel == SWE_KERNEL_NAIVE)
             e = launch_naive(c->dtype, c->state[in], c->state[outb], c->plane, c->nx, c->ny, c->pitch, c->dx, c->dy,
                              c->dt, c->g, s);
         else
@@ -289,6 +348,7 @@ swe_status swe_mass(swe_ctx *c, double *mass_out, void *stream)
 {
     if (!c || !mass_out) return SWE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SWE_TRY(sync_planes(c, s));
     SWE_TRY(launch_mass(c->dtype, plane_ptr(c, c->cur, 0), c->nx, c->ny, c->pitch, c->dx * c->dy, c->scratch,
                         c->result, s));
     SWE_TRY(cudaMemcpyAsync(c->host_result, c->result, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -301,6 +361,7 @@ swe_status swe_cfl_dt(swe_ctx *c, double cfl, double *dt_out, void *stream)
 {
     if (!c || !dt_out || !finite_pos(cfl)) return SWE_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SWE_TRY(sync_planes(c, s));
     SWE_TRY(launch_cfl(c->dtype, plane_ptr(c, c->cur, 0), plane_ptr(c, c->cur, 1), plane_ptr(c, c->cur, 2), c->nx,
                        c->ny, c->pitch, c->dx, c->dy, c->g, cfl, c->scratch, c->result, s));
     SWE_TRY(cudaMemcpyAsync(c->host_result, c->result, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -339,7 +400,10 @@ swe_status swe_query(swe_ctx *c, int key, long long *value)
         case SWE_Q_TILE_X: *value = c->kernel == SWE_KERNEL_NAIVE ? 64 : tiled_geom(c->dtype).tile_x; break;
         case SWE_Q_STEPS_PER_LAUNCH: *value = c->depth; break;
         case SWE_Q_TILE_Y: *value = c->kernel == SWE_KERNEL_NAIVE ? 4 : tiled_geom(c->dtype).tile_y; break;
-        case SWE_Q_STATE_PTR: *value = (long long)(uintptr_t)plane_ptr(c, c->cur, 0); break;
+        case SWE_Q_STATE_PTR:
+            // packed contexts: the packed state (h, hu, hv, 0 per cell)
+            *value = (long long)(uintptr_t)(c->kernel == SWE_KERNEL_PACKED ? c->packed[c->cur] : plane_ptr(c, c->cur, 0));
+            break;
         default: return SWE_EINVAL;
     }
     return SWE_OK;

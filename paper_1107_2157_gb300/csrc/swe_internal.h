@@ -37,6 +37,14 @@ cudaError_t launch_tiled(int dtype, const CUtensorMap *maps_in, void *out, size_
 cudaError_t launch_tb2(int dtype, int variant, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
                        long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
 void tb2_box(int dtype, int variant, int *bw, int *bh);  // TMA box of two-step kernel shape ``variant``
+// Packed-state kernel (swe_packed.cu): state as (h, hu, hv, 0) float4 cells,
+// ppitch cells per row.  launch_pack copies the planes into the packed
+// buffer (unpack = false) or back (unpack = true).
+cudaError_t launch_packed(const CUtensorMap *map, void *out, int nx, int ny, long long ppitch, double dx, double dy,
+                          double dt, double g, int *err, cudaStream_t s);
+cudaError_t launch_pack(const void *h, const void *u, const void *v, long long pitch, void *out, long long ppitch,
+                        int nx, int ny, bool unpack, cudaStream_t s);
+void packed_box(int *bw, int *bh);  // TMA box (cells) of the packed kernel
 StepGeom tiled_geom(int dtype);
 void tiled_box(int dtype, int *bw, int *bh);  // TMA box the tiled kernel loads
 
@@ -71,5 +79,7 @@ cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, i
 // if the driver entry point is unavailable or the encode fails.
 bool encode_plane_map(CUtensorMap *map, int dtype, const void *base, int nx, int ny, long long pitch, int box_x,
                       int box_y);
+// 3D map {4 components, nx, ny} over packed FP32 cells, ppitch cells per row.
+bool encode_packed_map(CUtensorMap *map, const void *base, int nx, int ny, long long ppitch, int box_x, int box_y);
 
 }  // namespace swe

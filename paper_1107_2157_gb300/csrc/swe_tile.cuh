@@ -26,6 +26,7 @@ struct TiledCfg {
     static constexpr int VX = VecOf<T>::N;  // cells per thread in x (16 bytes)
     static constexpr int TX = 32 * VX;      // tile width (one warp across)
     static constexpr int TY = NWARP * RY;   // tile height (warps stacked)
+    static constexpr int ROWS = RY;         // rows per warp
     static constexpr int AX = VX;           // x halo, rounded up to 16 bytes
     static constexpr int BW = TX + 2 * AX;  // TMA box width
     static constexpr int BH = TY + 2;       // TMA box height
@@ -48,6 +49,38 @@ __device__ __forceinline__ void load_row(const T *sH, const T *sU, const T *sV, 
     for (int p = 0; p < VX; ++p) c[p] = make_cell<T>(ph[p], pu[p], pv[p], hg);
 }
 
+// Shared-memory boxes as strip_compute reads them: three planes (SoA), or
+// one array of (h, hu, hv, pad) cells (the packed layout, FP32).  idx is a
+// cell index of the box.
+template <typename T>
+struct SoaBox {
+    const T *h, *u, *v;
+    template <int VX>
+    __device__ __forceinline__ void row(int idx, T hg, CellQ<T> (&c)[VX]) const
+    {
+        load_row<T, VX>(h, u, v, idx, hg, c);
+    }
+    __device__ __forceinline__ CellQ<T> cell(int idx, T hg) const { return make_cell<T>(h[idx], u[idx], v[idx], hg); }
+};
+
+struct PackedBox {
+    const float4 *p;
+    template <int VX>
+    __device__ __forceinline__ void row(int idx, float hg, CellQ<float> (&c)[VX]) const
+    {
+#pragma unroll
+        for (int q = 0; q < VX; ++q) {
+            const float4 s = p[idx + q];
+            c[q] = make_cell<float>(s.x, s.y, s.z, hg);
+        }
+    }
+    __device__ __forceinline__ CellQ<float> cell(int idx, float hg) const
+    {
+        const float4 s = p[idx];
+        return make_cell<float>(s.x, s.y, s.z, hg);
+    }
+};
+
 template <typename T, int VX>
 __device__ __forceinline__ void store_vec(T *dst, const T (&x)[VX])
 {
@@ -63,10 +96,10 @@ __device__ __forceinline__ void store_vec(T *dst, const T (&x)[VX])
 // where neighbours are formed (XEDGE: the tile touches an x-wall).  Rows
 // must lie inside the grid (0 <= y0 + r < ny).  ``store(r, h, hu, hv)``
 // receives each finished row.
-template <typename T, int VX, bool XEDGE, typename Store>
-__device__ __forceinline__ void strip_compute(const T *sH, const T *sU, const T *sV, int BW, int AX, int row_off,
-                                              int r_begin, int r_end, int cx, int gx, int nx, int ny, int y0,
-                                              const Coef<T> &k, Store &&store)
+template <typename T, int VX, bool XEDGE, typename Box, typename Store>
+__device__ __forceinline__ void strip_compute_box(const Box &box, int BW, int AX, int row_off, int r_begin, int r_end,
+                                                  int cx, int gx, int nx, int ny, int y0, const Coef<T> &k,
+                                                  Store &&store)
 {
     if (r_begin >= r_end) return;
     auto sidx = [&](int c, int r) { return (r + row_off) * BW + c + AX; };
@@ -75,12 +108,12 @@ __device__ __forceinline__ void strip_compute(const T *sH, const T *sU, const T 
     CellQ<T> cur[VX], nxt[VX];
     Flux3<T> gd[VX], gu[VX];
 
-    load_row<T, VX>(sH, sU, sV, sidx(cx, r_begin), k.hg, cur);
+    box.template row<VX>(sidx(cx, r_begin), k.hg, cur);
     if (y0 + r_begin == 0) {
 #pragma unroll
         for (int p = 0; p < VX; ++p) nxt[p] = mirror_y(cur[p]);
     } else {
-        load_row<T, VX>(sH, sU, sV, sidx(cx, r_begin - 1), k.hg, nxt);
+        box.template row<VX>(sidx(cx, r_begin - 1), k.hg, nxt);
     }
 #pragma unroll
     for (int p = 0; p < VX; ++p) gd[p] = yface_flux(nxt[p], cur[p], k);
@@ -92,15 +125,14 @@ __device__ __forceinline__ void strip_compute(const T *sH, const T *sU, const T 
 #pragma unroll
             for (int p = 0; p < VX; ++p) nxt[p] = mirror_y(cur[p]);
         } else {
-            load_row<T, VX>(sH, sU, sV, sidx(cx, r + 1), k.hg, nxt);
+            box.template row<VX>(sidx(cx, r + 1), k.hg, nxt);
         }
 #pragma unroll
         for (int p = 0; p < VX; ++p) gu[p] = yface_flux(cur[p], nxt[p], k);
 
         // x-neighbours of the thread's cells on row r
-        const int il = sidx(cx - 1, r), ir = sidx(cx + VX, r);
-        CellQ<T> left = make_cell<T>(sH[il], sU[il], sV[il], k.hg);
-        CellQ<T> right = make_cell<T>(sH[ir], sU[ir], sV[ir], k.hg);
+        CellQ<T> left = box.cell(sidx(cx - 1, r), k.hg);
+        CellQ<T> right = box.cell(sidx(cx + VX, r), k.hg);
         if (XEDGE) {
             if (gx == 0) left = mirror_x(cur[0]);
             if (pw == VX) right = mirror_x(cur[VX - 1]);
@@ -131,6 +163,15 @@ __device__ __forceinline__ void strip_compute(const T *sH, const T *sU, const T 
             gd[p] = gu[p];
         }
     }
+}
+
+template <typename T, int VX, bool XEDGE, typename Store>
+__device__ __forceinline__ void strip_compute(const T *sH, const T *sU, const T *sV, int BW, int AX, int row_off,
+                                              int r_begin, int r_end, int cx, int gx, int nx, int ny, int y0,
+                                              const Coef<T> &k, Store &&store)
+{
+    strip_compute_box<T, VX, XEDGE>(SoaBox<T>{sH, sU, sV}, BW, AX, row_off, r_begin, r_end, cx, gx, nx, ny, y0, k,
+                                    store);
 }
 
 // One cell of a box, computed on its own from the 5-point neighbourhood (the

@@ -300,3 +300,37 @@ def test_two_step_kernel_full_size_windows_against_oracle():
             sub = np.asarray(got[k][j0 - 1:j1, i0 - 1:i1], np.float64)
             err = np.abs(sub - ref[k]).max() / (scale_h if k == 0 else floor)
             assert err <= TOL_F32, (w, k, err)
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(1, 1, 3), (3, 5, 7), (130, 66, 10), (257, 129, 9), (128, 32, 6),
+                                         (300, 97, 11), (8, 200, 5), (1025, 40, 4)])
+def test_packed_kernel_equals_plane_kernel_bitwise(nx, ny, steps):
+    """The packed-state kernel ((h, hu, hv, 0) cells in one 16-byte vector)
+    runs the same strip routine on its box, so it gives the plane kernel's
+    bits, for ragged sizes with flow at every wall."""
+    s = si.smooth_flow_state(nx * 11 + ny, nx, ny).rounded_to(np.float32)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 0.8, 1.1, G, 0.3)
+    a = run_gpu(s, 0.8, 1.1, dt, G, steps, "f32", KERNELS["tiled"])
+    b = run_gpu(s, 0.8, 1.1, dt, G, steps, "f32", 4)
+    for k in range(3):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_packed_kernel_reductions_and_fp64_rejection():
+    """Mass and CFL of a packed context read the current (packed) state;
+    FP64 is not offered in the packed layout."""
+    from paper_1107_2157_gb300 import Grid, swe
+    s = si.smooth_flow_state(5, 200, 90).rounded_to(np.float32)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.3)
+    out = []
+    for kernel in (KERNELS["tiled"], 4):
+        with Grid(200, 90, 1.0, 1.0, dt, G, dtype="f32", kernel=kernel) as g:
+            g.set_state(*(a.astype(np.float32) for a in (s.h, s.hu, s.hv)))
+            m0 = g.mass()
+            g.step(7)
+            out.append((m0, g.mass(), g.cfl_dt(0.2), g.query(swe.SWE_Q_KERNEL)))
+    assert out[0][:3] == out[1][:3]
+    assert out[1][3] == 4
+    with pytest.raises(swe.SweError) as e:
+        Grid(16, 16, 1.0, 1.0, 0.01, G, dtype="f64", kernel=4)
+    assert e.value.status == swe.SWE_EUNSUPPORTED
