@@ -45,7 +45,9 @@ def parse():
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
     p.add_argument("--variant", type=int, default=None, help="two-step kernel tile shape 0..3 (with --kernel 3)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="grid", choices=["grid", "ensemble", "learned"],
+    p.add_argument("--px", type=int, default=2, help="partitioned: partitions along x")
+    p.add_argument("--py", type=int, default=2, help="partitioned: partitions along y")
+    p.add_argument("--workload", default="grid", choices=["grid", "ensemble", "learned", "partitioned"],
                    help="grid: one 8192^2 grid (default); ensemble: 512 uneven grids in one persistent launch; "
                         "learned: train the corrector and compare learned-coarse serving with plain fine runs")
     p.add_argument("--train-trajectories", type=int, default=1792)
@@ -599,6 +601,66 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# partitioned workload: the 8192^2 grid as px x py ghosted partitions on one
+# GPU (halo kernel + step kernel per step) next to the single-grid kernel
+# ---------------------------------------------------------------------------
+
+def run_partitioned(args):
+    import numpy as np
+    import torch
+
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import Grid, Partitioned, swe
+
+    torch.cuda.set_device(0)
+    n = args.n
+    st = si.large_grid_state(seed=1, n=n)
+    h = torch.from_numpy(st.h.astype(np.float32)).cuda()
+    z = torch.zeros_like(h)
+    del st
+    with Grid(n, n, 1.0, 1.0, 0.01, G, dtype="f32") as grid:
+        grid.set_state(h, z, z)
+        dt = grid.cfl_dt(CFL)
+    times = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Partitioned(n, n, args.px, args.py, 1.0, 1.0, dt, G) as p:
+        p.set_state(h, z, z)
+        p.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record()
+        p.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        times["partitioned"] = e0.elapsed_time(e1) / 1e3
+        halo = p.query(swe.SWE_PQ_HALO_CELLS)
+    with Grid(n, n, 1.0, 1.0, dt, G, dtype="f32") as grid:
+        grid.set_state(h, z, z)
+        grid.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record()
+        grid.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        times["single"] = e0.elapsed_time(e1) / 1e3
+    cells = n * n
+    peak, peak_kind = measured_peaks()
+    rate = cells * args.steps / times["partitioned"]
+    print(json.dumps({
+        "metric": METRIC, "workload": "partitioned", "value": rate, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * times["partitioned"] / args.steps, "dtype": "f32",
+        "data": "synthetic", "higher_is_better": True,
+        "config": {"workload": "8192x8192 FP32 grid (as the default workload) split into %d x %d ghosted "
+                               "partitions on one GPU; per step a halo launch and a step launch" % (args.px, args.py),
+                   "px": args.px, "py": args.py, "halo_cells_per_step": halo},
+        "single_grid": {"value": cells * args.steps / times["single"], "ms_per_step": 1e3 * times["single"] / args.steps},
+        "ratio_to_single_grid": times["single"] / times["partitioned"],
+        "roofline": {"bound": "hbm", "achieved": BYTES_PER_CELL_F32 * rate / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": BYTES_PER_CELL_F32 * rate / 1e9 / peak,
+                     "note": "24 B per cell-update over the whole step (halo + step launches)"},
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -607,6 +669,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "partitioned":
+        run_partitioned(args)
     else:
         run_ours(args)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:

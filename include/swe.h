@@ -286,6 +286,41 @@ typedef enum {
 swe_status swe_batch_query(swe_batch *b, int key, long long *value);
 
 /* ==========================================================================
+ * Domain decomposition.  One grid split into px x py partitions, each with a
+ * one-cell ghost ring, all on the current device: the layout a multi-GPU run
+ * would give each GPU (Sec. 4.1 and Fig. 1: MPI partitions of the global
+ * array with their halos, named there as future work), with the halo
+ * exchange done by a kernel.  Partition (a, b) holds columns
+ * [a nx / px, (a+1) nx / px) and rows [b ny / py, (b+1) ny / py) (integer
+ * division).  A step is a halo launch (ghosts next to another partition
+ * copy its edge cells; ghosts on the grid boundary are the reflective
+ * mirror of their own edge cell) and a step launch over all partitions
+ * (the single-grid kernel's TMA tiles, reading the ghost ring); the result
+ * equals swe_step on the whole grid bit for bit.  FP32.
+ * ========================================================================== */
+typedef struct swe_part swe_part;
+
+/* 1 <= px <= nx, 1 <= py <= ny, px * py <= 4096; spacing, dt, g > 0. */
+swe_status swe_part_create(int nx, int ny, int px, int py, double dx, double dy, double dt, double g,
+                           swe_part **out);
+void swe_part_destroy(swe_part *part);
+/* The whole nx x ny interior in or out (row stride ld >= nx floats, host or
+ * device pointers), scattered to / gathered from the partitions;
+ * stream-ordered. */
+swe_status swe_part_set_state(swe_part *part, const float *h, const float *hu, const float *hv, long long ld,
+                              void *stream);
+swe_status swe_part_get_state(swe_part *part, float *h, float *hu, float *hv, long long ld, void *stream);
+/* n_steps steps of every partition (two launches per step); stream-ordered. */
+swe_status swe_part_step(swe_part *part, int n_steps, void *stream);
+typedef enum {
+    SWE_PQ_PARTS = 0,      /* px * py */
+    SWE_PQ_HALO_CELLS = 1, /* ghost cells exchanged or mirrored per step (per field) */
+    SWE_PQ_LAUNCHES = 2,   /* launches enqueued so far */
+    SWE_PQ_ERROR = 3       /* the device error word (synchronous): 0 or SWE_ETIMEOUT */
+} swe_part_query_key;
+swe_status swe_part_query(swe_part *part, int key, long long *value);
+
+/* ==========================================================================
  * Learned coarse-grid corrector (no counterpart in the paper).  A network
  * of zero-padded 3x3 convolutions, 3 -> 32 -> 32 -> 3 channels with GELU
  * (0.5 z (1 + erf(z / sqrt 2))), BF16 weights and activations with FP32

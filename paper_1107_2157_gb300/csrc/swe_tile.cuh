@@ -96,7 +96,9 @@ __device__ __forceinline__ void store_vec(T *dst, const T (&x)[VX])
 // where neighbours are formed (XEDGE: the tile touches an x-wall).  Rows
 // must lie inside the grid (0 <= y0 + r < ny).  ``store(r, h, hu, hv)``
 // receives each finished row.
-template <typename T, int VX, bool XEDGE, typename Box, typename Store>
+// GHOSTED: the box's halo holds real neighbour cells everywhere (a
+// partition's ghost ring), so no wall is formed; use with XEDGE = false.
+template <typename T, int VX, bool XEDGE, typename Box, typename Store, bool GHOSTED = false>
 __device__ __forceinline__ void strip_compute_box(const Box &box, int BW, int AX, int row_off, int r_begin, int r_end,
                                                   int cx, int gx, int nx, int ny, int y0, const Coef<T> &k,
                                                   Store &&store)
@@ -109,7 +111,7 @@ __device__ __forceinline__ void strip_compute_box(const Box &box, int BW, int AX
     Flux3<T> gd[VX], gu[VX];
 
     box.template row<VX>(sidx(cx, r_begin), k.hg, cur);
-    if (y0 + r_begin == 0) {
+    if (!GHOSTED && y0 + r_begin == 0) {
 #pragma unroll
         for (int p = 0; p < VX; ++p) nxt[p] = mirror_y(cur[p]);
     } else {
@@ -121,7 +123,7 @@ __device__ __forceinline__ void strip_compute_box(const Box &box, int BW, int AX
 #pragma unroll 1
     for (int r = r_begin; r < r_end; ++r) {
         const int gy = y0 + r;
-        if (gy + 1 == ny) {
+        if (!GHOSTED && gy + 1 == ny) {
 #pragma unroll
             for (int p = 0; p < VX; ++p) nxt[p] = mirror_y(cur[p]);
         } else {
@@ -200,7 +202,7 @@ __device__ __forceinline__ void box_cell(const T *sH, const T *sU, const T *sV, 
 // Computes one output tile from the staged box (see TiledCfg; the box's
 // first row is tile row -ROW_OFF) and stores it.  Returns true if some
 // stored depth is not positive (h <= 0 or NaN).
-template <typename T, int NWARP, int RY, bool XEDGE, int ROW_OFF = 1>
+template <typename T, int NWARP, int RY, bool XEDGE, int ROW_OFF = 1, bool GHOSTED = false>
 __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T *sV, T *__restrict__ oH,
                                               T *__restrict__ oU, T *__restrict__ oV, int nx, int ny,
                                               long long pitch, int x0, int y0, const Coef<T> &k)
@@ -214,18 +216,19 @@ __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T 
     const int rb = warp * RY;
     const int re = min(rb + RY, ny - y0);
     bool bad = false;
-    strip_compute<T, VX, XEDGE>(sH, sU, sV, C::BW, C::AX, ROW_OFF, rb, re, cx, gx, nx, ny, y0, k,
-                                [&](int r, const T(&oh)[VX], const T(&ou)[VX], const T(&ov)[VX]) {
-                                    if (gx < nx) {
+    auto store_fn = [&](int r, const T(&oh)[VX], const T(&ou)[VX], const T(&ov)[VX]) {
+        if (gx < nx) {
 #pragma unroll
-                                        for (int p = 0; p < VX; ++p) bad |= (gx + p < nx) && !(oh[p] > T(0));
-                                        // whole 16-byte vectors: columns past nx land in the row padding
-                                        const size_t o = (size_t)(y0 + r) * (size_t)pitch + (size_t)gx;
-                                        store_vec<T, VX>(oH + o, oh);
-                                        store_vec<T, VX>(oU + o, ou);
-                                        store_vec<T, VX>(oV + o, ov);
-                                    }
-                                });
+            for (int p = 0; p < VX; ++p) bad |= (gx + p < nx) && !(oh[p] > T(0));
+            // whole 16-byte vectors: columns past nx land in the row padding
+            const size_t o = (size_t)(y0 + r) * (size_t)pitch + (size_t)gx;
+            store_vec<T, VX>(oH + o, oh);
+            store_vec<T, VX>(oU + o, ou);
+            store_vec<T, VX>(oV + o, ov);
+        }
+    };
+    strip_compute_box<T, VX, XEDGE, SoaBox<T>, decltype(store_fn) &, GHOSTED>(
+        SoaBox<T>{sH, sU, sV}, C::BW, C::AX, ROW_OFF, rb, re, cx, gx, nx, ny, y0, k, store_fn);
     return bad;
 }
 

@@ -27,6 +27,7 @@ SWE_FLAG_NONPOSITIVE, SWE_FLAG_MASS, SWE_FLAG_TIMEOUT, SWE_FLAG_FALLBACK = 1, 2,
  SWE_BQ_VARIANT_COUNT) = range(13)
 (SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
  SWE_Q_STATE_PTR, SWE_Q_STEPS_PER_LAUNCH) = range(8)
+SWE_PQ_PARTS, SWE_PQ_HALO_CELLS, SWE_PQ_LAUNCHES, SWE_PQ_ERROR = range(4)
 
 
 class SweError(RuntimeError):
@@ -92,6 +93,12 @@ _SIGS = {
     "swe_batch_learned_step": (_i, [_vp, _vp, _i, _i, _vp]),
     "swe_net_set_loss_weighting": (_i, [_vp, ctypes.c_float, ctypes.c_float]),
     "swe_resample": (_i, [_vp, _ll, _ll, _ll, _i, _i, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
+    "swe_part_create": (_i, [_i, _i, _i, _i, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
+    "swe_part_destroy": (None, [_vp]),
+    "swe_part_set_state": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
+    "swe_part_get_state": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
+    "swe_part_step": (_i, [_vp, _i, _vp]),
+    "swe_part_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_selftest_gelu": (_i, [_vp, _vp, _i, _i, _vp]),
     "swe_downsample": (_i, [_i, _vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
@@ -293,6 +300,59 @@ class Grid:
 
     def query(self, key):
         return swe_query(self.ctx, key)
+
+
+# --- domain decomposition on one device -------------------------------------------------------
+
+class Partitioned:
+    """One FP32 grid split into px x py ghosted partitions (owns a swe_part)."""
+
+    def __init__(self, nx, ny, px, py, dx, dy, dt, g):
+        h = _vp()
+        check(lib().swe_part_create(int(nx), int(ny), int(px), int(py), dx, dy, dt, g, ctypes.byref(h)),
+              "swe_part_create")
+        self.p = h.value
+        self.nx, self.ny = nx, ny
+
+    def close(self):
+        if getattr(self, "p", None):
+            lib().swe_part_destroy(self.p)
+            self.p = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, h, hu, hv, stream=None):
+        bufs = [_buf(a, np.float32) for a in (h, hu, hv)]
+        check(lib().swe_part_set_state(self.p, bufs[0][0], bufs[1][0], bufs[2][0], bufs[0][1],
+                                       stream if stream is not None else current_stream()), "swe_part_set_state")
+
+    def get_state(self, stream=None):
+        out = [np.empty((self.ny, self.nx), np.float32) for _ in range(3)]
+        bufs = [_buf(a, np.float32) for a in out]
+        check(lib().swe_part_get_state(self.p, bufs[0][0], bufs[1][0], bufs[2][0], bufs[0][1],
+                                       stream if stream is not None else current_stream()), "swe_part_get_state")
+        import torch
+        torch.cuda.synchronize()
+        return out
+
+    def step(self, n, stream=None):
+        check(lib().swe_part_step(self.p, int(n), stream if stream is not None else current_stream()),
+              "swe_part_step")
+
+    def query(self, key):
+        v = _ll()
+        check(lib().swe_part_query(self.p, int(key), ctypes.byref(v)), "swe_part_query")
+        return v.value
 
 
 # --- batched ensembles ----------------------------------------------------------------------

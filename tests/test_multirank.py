@@ -1,6 +1,7 @@
-"""The multi-GPU path of bench.py runs independent replicas (the grids do
-not exchange data); across ranks only the timings meet, as a max.  Checked
-here with two gloo ranks on the CPU."""
+"""Multi-process logic on the CPU (gloo): the replicas of bench.py meet only
+in their timings (a max over ranks); a grid decomposed across ranks
+exchanges one-cell halo strips with its neighbours and gives the
+single-domain result bit for bit."""
 import os
 import socket
 import sys
@@ -55,3 +56,84 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.aggregate_over_ranks([3.0, 1.0], 1) == [3.0, 1.0]
     assert bench.whole_job_rate(1, 100, 4, 2.0) == 200.0
+
+
+def _halo_rank(rank, world, port, px, py, nx, ny, steps, out):
+    """One partition per rank: exchange the halo over gloo, then one oracle
+    step (FP64) on the ghosted arrays, ``steps`` times; the interior goes
+    back to the parent."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import oracle
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import partition as P
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        s = si.smooth_flow_state(3, nx, ny)
+        dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, 9.8, 0.3)
+        a, b = P.coords(rank, px)
+        x0, x1 = P.bounds(nx, px, a)
+        y0, y1 = P.bounds(ny, py, b)
+        fields = []
+        for full in (s.h, s.hu, s.hv):
+            F = torch.zeros((y1 - y0 + 2, x1 - x0 + 2), dtype=torch.float64)
+            F[1:-1, 1:-1] = torch.from_numpy(np.ascontiguousarray(full[y0:y1, x0:x1]))
+            fields.append(F)
+        for _ in range(steps):
+            P.exchange_halo(fields, rank, px, py)
+            (oH, oU, oV), _, _ = oracle.step_padded(*(np.ascontiguousarray(F.numpy()) for F in fields),
+                                                    1.0, 1.0, dt, 9.8)
+            fields = [torch.from_numpy(x) for x in (oH, oU, oV)]
+        out[rank] = [F[1:-1, 1:-1].numpy().copy() for F in fields]
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("px,py", [(2, 2), (3, 1), (1, 3)])
+def test_gloo_ranks_with_halo_exchange_equal_the_single_domain_bitwise(px, py):
+    """Partitions on separate processes, ghost strips exchanged with
+    torch.distributed (gloo), each stepped by the FP64 oracle: the gathered
+    state equals the oracle on the whole grid bit for bit, walls included."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import oracle
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import partition as P
+    nx, ny, steps, world = 37, 23, 6, px * py
+    ctx = mp.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_halo_rank, args=(r, world, port, px, py, nx, ny, steps, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(180)
+    assert all(p.exitcode == 0 for p in procs)
+    s = si.smooth_flow_state(3, nx, ny)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, 9.8, 0.3)
+    ref = oracle.run(s.h, s.hu, s.hv, 1.0, 1.0, dt, 9.8, steps)
+    got = [np.zeros((ny, nx)) for _ in range(3)]
+    for r in range(world):
+        a, b = P.coords(r, px)
+        x0, x1 = P.bounds(nx, px, a)
+        y0, y1 = P.bounds(ny, py, b)
+        for k in range(3):
+            got[k][y0:y1, x0:x1] = out[r][k]
+    for k in range(3):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_partition_layout_covers_the_grid_once():
+    sys.path.insert(0, ROOT)
+    from paper_1107_2157_gb300 import partition as P
+    for n, p in ((37, 3), (8, 8), (1000, 7)):
+        spans = [P.bounds(n, p, a) for a in range(p)]
+        assert spans[0][0] == 0 and spans[-1][1] == n
+        assert all(spans[i][1] == spans[i + 1][0] and spans[i][1] > spans[i][0] for i in range(p - 1))
+    nb = P.neighbours(4, 3, 3)  # the centre of a 3 x 3 layout
+    assert nb == {P.LEFT: 3, P.RIGHT: 5, P.BOTTOM: 1, P.TOP: 7}
+    assert P.neighbours(0, 3, 3) == {P.LEFT: None, P.RIGHT: 1, P.BOTTOM: None, P.TOP: 3}
