@@ -38,7 +38,8 @@ UNIT = "cell-updates/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 1000 for the grid, 500 for the ensemble)")
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
@@ -59,7 +60,10 @@ def parse():
     p.add_argument("--skip-train", action="store_true",
                    help="learned: serve with untrained weights (kernel timing and profiling only)")
     p.add_argument("--tune-cache", default=None)
-    return p.parse_args()
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = 500 if a.workload == "ensemble" else 1000
+    return a
 
 
 def dist_env():
