@@ -321,6 +321,65 @@ typedef enum {
 swe_status swe_part_query(swe_part *part, int key, long long *value);
 
 /* ==========================================================================
+ * Region front end (Sec. 2.3 region functions; Sec. 3.1 statements; Sec.
+ * 4.2.1 lowering).  The step and the wall fill written as array statements
+ * over halo regions (region_cpy / region_ptr with halo [left, right, down,
+ * up]) in a C++ expression-template header, each statement lowered to a
+ * loop of a CTA's threads over the statement's region, with the inputs
+ * staged in shared memory by TMA.  Every operation of a statement is one
+ * IEEE round-to-nearest operation in the stated order (no FMA contraction,
+ * IEEE division), so an FP64 step equals the FP64 oracle bit for bit.
+ *
+ * Arrays are device planes of (nx + 2) x (ny + 2) elements with the ghost
+ * ring, row stride ``pitch`` elements (pitch >= nx + 2, pitch * element size
+ * a multiple of 16 bytes, planes 16-byte aligned), interior cell (i, j),
+ * 1 <= i <= nx, 1 <= j <= ny, at j * pitch + i.  The caller owns them.
+ * As in Sec. 2.3 the step leaves boundary conditions to the caller: it reads
+ * the ghosts as they are, and swe_region_walls fills them.
+ * ========================================================================== */
+typedef struct swe_region swe_region;
+
+/* dtype SWE_F32 or SWE_F64; 1 <= nx, ny <= 65536; variant 0 (default: FP32
+ * 3, FP64 2) or a tile shape, cells per CTA / threads: FP32 1..5 =
+ * 64x16/256, 128x8/256, 32x32/256, 64x16/128, 32x16/128; FP64 1..3 =
+ * 64x8/256, 32x16/256, 32x8/128.  SWE_EINVAL for anything else. */
+swe_status swe_region_create(int dtype, int nx, int ny, long long pitch, int variant, swe_region **out);
+void swe_region_destroy(swe_region *r);
+/* One step: in[0..2] = H, U, V with ghosts filled, out[0..2] receive the
+ * interior (their ghosts are not written; out must not alias in).
+ * Stream-ordered; SWE_EINVAL for NULL or misaligned planes or a
+ * non-positive dx, dy, dt or g. */
+swe_status swe_region_step(swe_region *r, const void *const in[3], void *const out[3], double dx, double dy,
+                           double dt, double g, void *stream);
+/* Reflective ghost fill of the sides in ``walls`` (1 left, 2 right,
+ * 4 bottom, 8 top): ghost = the adjacent interior cell, wall-normal
+ * momentum negated; corner ghosts untouched.  Stream-ordered. */
+swe_status swe_region_walls(swe_region *r, void *const state[3], int walls, void *stream);
+/* n_steps of (walls, step), alternating between a and b starting from a;
+ * *result_in_b (if not NULL) is 1 when the final state is in b. */
+swe_status swe_region_run(swe_region *r, void *const a[3], void *const b[3], int n_steps, int walls, double dx,
+                          double dy, double dt, double g, void *stream, int *result_in_b);
+typedef enum {
+    SWE_RQ_LAUNCHES = 0, /* launches enqueued so far */
+    SWE_RQ_TILE_X = 1,   /* interior cells per CTA in x */
+    SWE_RQ_TILE_Y = 2,   /* ... in y */
+    SWE_RQ_SMEM = 3,     /* dynamic shared memory per CTA, bytes */
+    SWE_RQ_ERROR = 4     /* the device error word (synchronous): 0, SWE_EINVAL (a
+                            statement whose regions do not conform) or SWE_ETIMEOUT */
+} swe_region_query_key;
+swe_status swe_region_query(swe_region *r, int key, long long *value);
+/* Host only, evaluates nothing: the extents (x, y) the statement groups of
+ * the step and the wall fill take on nx x ny interior cells, in order:
+ * cell fluxes, x-faces, y-faces, update, then the left, right, bottom and top ghost
+ * strips.  ext receives 2 * min(*n_groups, max_groups) ints; an extent of a
+ * group whose regions do not conform is negative. */
+swe_status swe_region_shapes(int nx, int ny, int *ext, int max_groups, int *n_groups);
+/* Self-test of the FP32 division of the region statements: out[i] =
+ * a[i] / b[i] correctly rounded, by the statements' FMA division (which = 0)
+ * or by CUDA's __fdiv_rn (1); device pointers, n >= 0; stream-ordered. */
+swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, int which, void *stream);
+
+/* ==========================================================================
  * Learned coarse-grid corrector (no counterpart in the paper).  A network
  * of zero-padded 3x3 convolutions, 3 -> 32 -> 32 -> 3 channels with GELU
  * (0.5 z (1 + erf(z / sqrt 2))), BF16 weights and activations with FP32

@@ -5,6 +5,8 @@ Plain, slow, FP64 code that states what the GPU path must compute:
     update of the two-step Lax-Wendroff scheme (Sec. 3, step equations;
     Sec. 3.1, Fortran statements) -- in ``swe_oracle.c``;
   * the FP64 mass and CFL time step (Sec. 3) -- in ``swe_oracle.c``;
+  * the same step and wall fill in binary32, the paper's precision -- in
+    ``swe_oracle_f32.c``;
   * the block-average restriction and the corrector network -- in
     ``nn.py`` (numpy, FP64); the learned coarse step built from them and
     the Lax-Wendroff step -- in ``learned.py``.
@@ -28,6 +30,7 @@ WALL_ALL = 15
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 def lib():
@@ -49,6 +52,11 @@ def lib():
         L.oracle_mass.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
         L.oracle_cfl_dt.restype = ctypes.c_double
         L.oracle_cfl_dt.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [_dp] * 3
+        L.oracle_fill_halo_f32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, _fp]
+        L.oracle_step_f32.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [_fp] * 7
+        L.oracle_run_f32.restype = ctypes.c_int
+        L.oracle_run_f32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 \
+            + [ctypes.c_int, _fp, _fp, _fp]
         _lib = L
     return _lib
 
@@ -104,6 +112,43 @@ def run_padded(H, U, V, dx, dy, dt, g, n_steps, walls=WALL_ALL):
         raise MemoryError("oracle_run could not allocate its buffers")
 
 
+def _ptr32(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_fp)
+
+
+def fill_halo_f32(H: np.ndarray, U: np.ndarray, V: np.ndarray, walls: int = WALL_ALL) -> None:
+    """The reflective ghost fill on padded float32 arrays."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    lib().oracle_fill_halo_f32(nx, ny, walls, _ptr32(H), _ptr32(U), _ptr32(V))
+
+
+def step_padded_f32(H, U, V, dx, dy, dt, g):
+    """One binary32 step (the paper's precision) on padded float32 arrays
+    whose ghost ring is filled; returns the padded outputs (ghosts zero)."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    L = lib()
+    out = [np.zeros_like(H) for _ in range(3)]
+    faces = np.zeros(L.oracle_face_workspace(nx, ny), dtype=np.float32)
+    L.oracle_step_f32(nx, ny, dx, dy, dt, g, _ptr32(H), _ptr32(U), _ptr32(V),
+                      _ptr32(out[0]), _ptr32(out[1]), _ptr32(out[2]), _ptr32(faces))
+    return out
+
+
+def run_f32(h, hu, hv, dx, dy, dt, g, n_steps, walls=WALL_ALL):
+    """n_steps in binary32 with reflective walls on interior arrays (values
+    rounded to float32 first); returns float32 interiors."""
+    P = []
+    for a in (h, hu, hv):
+        p = np.zeros((a.shape[0] + 2, a.shape[1] + 2), np.float32)
+        p[1:-1, 1:-1] = np.asarray(a, np.float32)
+        P.append(p)
+    ny, nx = P[0].shape[0] - 2, P[0].shape[1] - 2
+    if lib().oracle_run_f32(nx, ny, walls, dx, dy, dt, g, int(n_steps), *(_ptr32(p) for p in P)) != 0:
+        raise MemoryError("oracle_run_f32 could not allocate its buffers")
+    return tuple(p[1:-1, 1:-1].copy() for p in P)
+
+
 def run(h, hu, hv, dx, dy, dt, g, n_steps):
     """n_steps with reflective walls on interior arrays; returns interiors."""
     H, U, V = pad(np.asarray(h, np.float64)), pad(np.asarray(hu, np.float64)), pad(np.asarray(hv, np.float64))
@@ -126,7 +171,7 @@ def cfl_dt(h, hu, hv, dx, dy, g, cfl) -> float:
 
 def run_window(ic: Callable[[Tuple[int, int, int, int]], Tuple[np.ndarray, np.ndarray, np.ndarray]],
                nx: int, ny: int, window: Tuple[int, int, int, int],
-               dx, dy, dt, g, n_steps):
+               dx, dy, dt, g, n_steps, binary32: bool = False):
     """Exact values on a window of a large grid after n_steps.
 
     The scheme reads only the four edge neighbours of a cell, so after n
@@ -137,6 +182,7 @@ def run_window(ic: Callable[[Tuple[int, int, int, int]], Tuple[np.ndarray, np.nd
     values on sides that are not walls, and the ordinary step runs on it with
     reflective fill on the wall sides only.  Cells inside ``window`` are then
     exactly those of the full-grid run (checked bitwise in the tests).
+    ``binary32`` runs the binary32 step instead of the FP64 one.
     Returns (h, hu, hv) on the window, shape (j1-j0+1, i1-i0+1).
     """
     i0, i1, j0, j1 = window
@@ -149,7 +195,12 @@ def run_window(ic: Callable[[Tuple[int, int, int, int]], Tuple[np.ndarray, np.nd
     walls |= WALL_BOTTOM if c == 1 else 0
     walls |= WALL_TOP if d == ny else 0
     fields = ic((a - 1, b + 1, c - 1, d + 1))
-    H, U, V = (np.ascontiguousarray(f, dtype=np.float64) for f in fields)
-    run_padded(H, U, V, dx, dy, dt, g, n, walls)
+    if binary32:
+        H, U, V = (np.ascontiguousarray(f, dtype=np.float32) for f in fields)
+        if lib().oracle_run_f32(b - a + 1, d - c + 1, walls, dx, dy, dt, g, n, _ptr32(H), _ptr32(U), _ptr32(V)):
+            raise MemoryError("oracle_run_f32 could not allocate its buffers")
+    else:
+        H, U, V = (np.ascontiguousarray(f, dtype=np.float64) for f in fields)
+        run_padded(H, U, V, dx, dy, dt, g, n, walls)
     sl = (slice(j0 - c + 1, j1 - c + 2), slice(i0 - a + 1, i1 - a + 2))
     return H[sl].copy(), U[sl].copy(), V[sl].copy()

@@ -28,6 +28,7 @@ SWE_FLAG_NONPOSITIVE, SWE_FLAG_MASS, SWE_FLAG_TIMEOUT, SWE_FLAG_FALLBACK = 1, 2,
 (SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
  SWE_Q_STATE_PTR, SWE_Q_STEPS_PER_LAUNCH) = range(8)
 SWE_PQ_PARTS, SWE_PQ_HALO_CELLS, SWE_PQ_LAUNCHES, SWE_PQ_ERROR = range(4)
+SWE_RQ_LAUNCHES, SWE_RQ_TILE_X, SWE_RQ_TILE_Y, SWE_RQ_SMEM, SWE_RQ_ERROR = range(5)
 
 
 class SweError(RuntimeError):
@@ -99,7 +100,16 @@ _SIGS = {
     "swe_part_get_state": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
     "swe_part_step": (_i, [_vp, _i, _vp]),
     "swe_part_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
+    "swe_region_create": (_i, [_i, _i, _i, _ll, _i, ctypes.POINTER(_vp)]),
+    "swe_region_destroy": (None, [_vp]),
+    "swe_region_step": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _d, _d, _d, _vp]),
+    "swe_region_walls": (_i, [_vp, ctypes.POINTER(_vp), _i, _vp]),
+    "swe_region_run": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _d, _d, _d, _d, _vp,
+                            ctypes.POINTER(_i)]),
+    "swe_region_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
+    "swe_region_shapes": (_i, [_i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
     "swe_selftest_gelu": (_i, [_vp, _vp, _i, _i, _vp]),
+    "swe_selftest_div": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "swe_downsample": (_i, [_i, _vp, _ll, _ll, _ll, _vp, _ll, _ll, _ll, _i, _i, _i, _vp]),
 }
 
@@ -352,6 +362,81 @@ class Partitioned:
     def query(self, key):
         v = _ll()
         check(lib().swe_part_query(self.p, int(key), ctypes.byref(v)), "swe_part_query")
+        return v.value
+
+
+# --- region front end ----------------------------------------------------------------------
+
+def swe_region_shapes(nx, ny):
+    """Extents (x, y) of the step's and the wall fill's statement groups on
+    nx x ny interior cells (host only; nothing is evaluated)."""
+    ext = (_i * 32)()
+    n = _i()
+    check(lib().swe_region_shapes(int(nx), int(ny), ext, 16, ctypes.byref(n)), "swe_region_shapes")
+    return [(ext[2 * k], ext[2 * k + 1]) for k in range(min(n.value, 16))]
+
+
+def _ptr3(planes):
+    return (_vp * 3)(*[int(p.data_ptr()) if hasattr(p, "data_ptr") else int(p) for p in planes])
+
+
+class Region:
+    """The step written as region statements (owns a swe_region).  State
+    triples are caller-owned device planes of (ny + 2) rows x ``pitch``
+    elements with the ghost ring (torch tensors or raw pointers)."""
+
+    def __init__(self, dtype, nx, ny, pitch=None, variant=0):
+        es = 8 if dtype == SWE_F64 else 4
+        if pitch is None:
+            pitch = ((nx + 2) * es + 127) // 128 * 128 // es
+        h = _vp()
+        check(lib().swe_region_create(int(dtype), int(nx), int(ny), int(pitch), int(variant), ctypes.byref(h)),
+              "swe_region_create")
+        self.r = h.value
+        self.dtype, self.nx, self.ny, self.pitch = dtype, nx, ny, pitch
+
+    def planes(self):
+        """Three zeroed (ny + 2) x pitch device planes (torch)."""
+        import torch
+        t = torch.float64 if self.dtype == SWE_F64 else torch.float32
+        return [torch.zeros((self.ny + 2, self.pitch), dtype=t, device="cuda") for _ in range(3)]
+
+    def close(self):
+        if getattr(self, "r", None):
+            lib().swe_region_destroy(self.r)
+            self.r = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, src, dst, dx, dy, dt, g, stream=None):
+        check(lib().swe_region_step(self.r, _ptr3(src), _ptr3(dst), dx, dy, dt, g,
+                                    stream if stream is not None else current_stream()), "swe_region_step")
+
+    def walls(self, state, walls=15, stream=None):
+        check(lib().swe_region_walls(self.r, _ptr3(state), int(walls),
+                                     stream if stream is not None else current_stream()), "swe_region_walls")
+
+    def run(self, a, b, n_steps, dx, dy, dt, g, walls=15, stream=None):
+        """n_steps of (walls, step) from a; returns 1 if the result is in b."""
+        in_b = _i()
+        check(lib().swe_region_run(self.r, _ptr3(a), _ptr3(b), int(n_steps), int(walls), dx, dy, dt, g,
+                                   stream if stream is not None else current_stream(), ctypes.byref(in_b)),
+              "swe_region_run")
+        return in_b.value
+
+    def query(self, key):
+        v = _ll()
+        check(lib().swe_region_query(self.r, int(key), ctypes.byref(v)), "swe_region_query")
         return v.value
 
 
