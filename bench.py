@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--px", type=int, default=2, help="partitioned: partitions along x")
     p.add_argument("--py", type=int, default=2, help="partitioned: partitions along y")
     p.add_argument("--region-variant", type=int, default=0, help="region: tile shape (0 = default)")
+    p.add_argument("--region-bed", action="store_true",
+                   help="region: the topography variant (bed mounds, left/right sides open, bottom/top walls)")
     p.add_argument("--workload", default="grid", choices=["grid", "ensemble", "learned", "partitioned", "region"],
                    help="grid: one 8192^2 grid (default); ensemble: 512 uneven grids in one persistent launch; "
                         "learned: train the corrector and compare learned-coarse serving with plain fine runs")
@@ -119,6 +121,9 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "region_lw_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_region.cu", "paper_1107_2157_gb300/csrc/swe_region.cuh",
                                 "paper_1107_2157_gb300/csrc/swe_device.cuh"),
+    "region_lw_kernel<float, bed>": ("paper_1107_2157_gb300/csrc/swe_region.cu",
+                                     "paper_1107_2157_gb300/csrc/swe_region.cuh",
+                                     "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "lw_tiled_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_step.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
                                "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "lw_packed_kernel": ("paper_1107_2157_gb300/csrc/swe_packed.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
@@ -682,7 +687,8 @@ def run_region(args):
 
     torch.cuda.set_device(0)
     n = args.n
-    st = si.large_grid_state(seed=1, n=n)
+    bed_mode = args.region_bed
+    st = si.large_grid_bed_state(n=n) if bed_mode else si.large_grid_state(seed=1, n=n)
     h = torch.from_numpy(st.h.astype(np.float32)).cuda()
     z = torch.zeros_like(h)
     del st
@@ -692,10 +698,17 @@ def run_region(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    kinds = (2, 2, 1, 1) if bed_mode else (1, 1, 1, 1)
     with Region(swe.SWE_F32, n, n, variant=args.region_variant) as reg:
         a, b = reg.planes(), reg.planes()
+        bed = None
+        if bed_mode:
+            bed = reg.planes()[0]
+            bed[1:-1, 1:n + 1] = torch.from_numpy(si.large_grid_bed(n=n).astype(np.float32)).cuda()
+            bed[0], bed[-1] = bed[1], bed[-2]
+            bed[:, 0], bed[:, n + 1] = bed[:, 1], bed[:, n]
         a[0][1:-1, 1:n + 1] = h
-        reg.run(a, b, args.warmup, 1.0, 1.0, dt, G, stream=sp)
+        reg.run_bc(a, b, args.warmup, 1.0, 1.0, dt, G, kinds=kinds, bed=bed, stream=sp)
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
         time.sleep(0.3)
@@ -706,7 +719,7 @@ def run_region(args):
         e0, e1 = ev(), ev()
         l0 = reg.query(swe.SWE_RQ_LAUNCHES)
         e0.record(stream)
-        in_b = reg.run(a, b, args.steps, 1.0, 1.0, dt, G, stream=sp)
+        in_b = reg.run_bc(a, b, args.steps, 1.0, 1.0, dt, G, kinds=kinds, bed=bed, stream=sp)
         e1.record(stream)
         torch.cuda.synchronize()
         t_run = e0.elapsed_time(e1) / 1e3
@@ -718,7 +731,11 @@ def run_region(args):
         s0, s1 = ev(), ev()
         s0.record(stream)
         for i in range(k):
-            reg.step(a if i % 2 == 0 else b, b if i % 2 == 0 else a, 1.0, 1.0, dt, G, stream=sp)
+            src, dst = (a, b) if i % 2 == 0 else (b, a)
+            if bed_mode:
+                reg.step_bed(src, bed, dst, 1.0, 1.0, dt, G, stream=sp)
+            else:
+                reg.step(src, dst, 1.0, 1.0, dt, G, stream=sp)
         s1.record(stream)
         torch.cuda.synchronize()
         t_launch = s0.elapsed_time(s1) / 1e3 / k
@@ -739,23 +756,32 @@ def run_region(args):
     cells = n * n
     peak, peak_kind = measured_peaks()
     rate = cells * args.steps / t_run
-    achieved = BYTES_PER_CELL_F32 * cells / t_launch / 1e9
+    bpc = BYTES_PER_CELL_F32 + (4 if bed_mode else 0)  # the bed plane is read too
+    achieved = bpc * cells / t_launch / 1e9
+    kname = "region_lw_kernel<float, bed>" if bed_mode else "region_lw_kernel<float>"
+    if bed_mode:
+        wl = ("%dx%d FP32, the default workload's surface (1 + 64 bumps) over 32 Gaussian bed mounds (depth = "
+              "surface - bed, at rest), stepped by the region-statement kernels with the bed-slope source; left and "
+              "right sides open, bottom and top reflective; a boundary launch and a step launch per step" % (n, n))
+    else:
+        wl = ("%dx%d FP32 grid, 64 Gaussian bumps at rest (as the default workload), stepped by the region-statement "
+              "kernels: a wall-fill launch and a step launch per step on ghosted planes; every statement operation "
+              "IEEE round-to-nearest" % (n, n))
     print(json.dumps({
-        "metric": METRIC, "workload": "region", "value": rate, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "workload": "region_bed" if bed_mode else "region", "value": rate, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_run / args.steps, "dtype": "f32", "data": "synthetic",
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "config": {"workload": "%dx%d FP32 grid, 64 Gaussian bumps at rest (as the default workload), stepped by "
-                               "the region-statement kernels: a wall-fill launch and a step launch per step on "
-                               "ghosted planes; every statement operation IEEE round-to-nearest" % (n, n),
-                   "tile": tile, "l2": "inputs (3 planes, %d MB) larger than L2" % (12 * cells // 2 ** 20)},
+        "config": {"workload": wl, "tile": tile,
+                   "l2": "inputs (%d planes, %d MB) larger than L2" % (4 if bed_mode else 3,
+                                                                        (16 if bed_mode else 12) * cells // 2 ** 20)},
         "hand_kernel": {"value": cells * args.steps / t_hand, "ms_per_step": 1e3 * t_hand / args.steps},
         "ratio_to_hand_kernel": t_hand / t_run,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic_per_launch("region_lw_kernel<float>", cells),
-                     "kernel": "region_lw_kernel<float> (1 step per launch)",
+                     "traffic": traffic_per_launch(kname, cells),
+                     "kernel": kname + " (1 step per launch)",
                      "note": "HBM is the algorithmic bound; the kernel measures instruction-issue bound (IEEE "
                              "division and the statement loops over shared-memory temporaries)",
-                     "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_F32, "launch_ms": t_launch * 1e3,
+                     "algorithmic_bytes_per_cell_update": bpc, "launch_ms": t_launch * 1e3,
                      "peak_source": peak_kind + " hbm_gbs (copy)"},
         "gpu_launches": int(launches),
         "clocks": clocks,

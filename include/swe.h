@@ -351,14 +351,37 @@ void swe_region_destroy(swe_region *r);
  * non-positive dx, dy, dt or g. */
 swe_status swe_region_step(swe_region *r, const void *const in[3], void *const out[3], double dx, double dy,
                            double dt, double g, void *stream);
+/* One step over a bottom topography (no counterpart in the paper, whose
+ * bed is flat): ``bed`` is the bed elevation B, a plane like the state's
+ * with its ghost ring filled (for walls and open sides alike the ghost
+ * copies the edge cell), H the water depth and H + B the free surface.  The
+ * momentum rows gain the bed-slope source -g H B_x, -g H B_y, taken at the
+ * points of the pressure-flux difference it balances with the depth
+ * averaged over the same two points (step 1: + dt/2dx g (H_a + H_b)/2
+ * (B_a - B_b) on the face between cells a, b; step 2: + dt/dx g (Hx_L +
+ * Hx_R)/2 (Bx_L - Bx_R) with Bx the mean of the two cells beside a face;
+ * likewise in y), so a lake at rest (H + B constant, no flow) stays at
+ * rest.  Otherwise as swe_region_step. */
+swe_status swe_region_step_bed(swe_region *r, const void *const in[3], const void *bed, void *const out[3], double dx,
+                               double dy, double dt, double g, void *stream);
 /* Reflective ghost fill of the sides in ``walls`` (1 left, 2 right,
  * 4 bottom, 8 top): ghost = the adjacent interior cell, wall-normal
  * momentum negated; corner ghosts untouched.  Stream-ordered. */
 swe_status swe_region_walls(swe_region *r, void *const state[3], int walls, void *stream);
+/* Ghost fill with a kind per side (kinds[0..3] = left, right, bottom, top):
+ * 0 leaves the side alone, 1 reflective wall (as swe_region_walls), 2 open
+ * (zero-gradient: the ghost copies the adjacent interior cell, all three
+ * components, so waves leave the domain).  SWE_EINVAL for another kind. */
+swe_status swe_region_boundary(swe_region *r, void *const state[3], const int kinds[4], void *stream);
 /* n_steps of (walls, step), alternating between a and b starting from a;
  * *result_in_b (if not NULL) is 1 when the final state is in b. */
 swe_status swe_region_run(swe_region *r, void *const a[3], void *const b[3], int n_steps, int walls, double dx,
                           double dy, double dt, double g, void *stream, int *result_in_b);
+/* As swe_region_run with per-side boundary kinds (swe_region_boundary) and,
+ * if ``bed`` is not NULL, the step over that bed (swe_region_step_bed). */
+swe_status swe_region_run_bc(swe_region *r, void *const a[3], void *const b[3], const void *bed, int n_steps,
+                             const int kinds[4], double dx, double dy, double dt, double g, void *stream,
+                             int *result_in_b);
 typedef enum {
     SWE_RQ_LAUNCHES = 0, /* launches enqueued so far */
     SWE_RQ_TILE_X = 1,   /* interior cells per CTA in x */

@@ -7,6 +7,9 @@ Plain, slow, FP64 code that states what the GPU path must compute:
   * the FP64 mass and CFL time step (Sec. 3) -- in ``swe_oracle.c``;
   * the same step and wall fill in binary32, the paper's precision -- in
     ``swe_oracle_f32.c``;
+  * open (transmissive) sides and the step with a bed-slope source over a
+    bottom topography, two variants the paper leaves open -- in
+    ``swe_oracle_bathy.c``;
   * the block-average restriction and the corrector network -- in
     ``nn.py`` (numpy, FP64); the learned coarse step built from them and
     the Lax-Wendroff step -- in ``learned.py``.
@@ -57,6 +60,10 @@ def lib():
         L.oracle_run_f32.restype = ctypes.c_int
         L.oracle_run_f32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 \
             + [ctypes.c_int, _fp, _fp, _fp]
+        L.oracle_fill_open.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.oracle_step_bathy.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [_dp] * 8
+        L.oracle_run_bc.restype = ctypes.c_int
+        L.oracle_run_bc.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 4 + [ctypes.c_int, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -149,6 +156,45 @@ def run_f32(h, hu, hv, dx, dy, dt, g, n_steps, walls=WALL_ALL):
     return tuple(p[1:-1, 1:-1].copy() for p in P)
 
 
+def fill_open(H: np.ndarray, U: np.ndarray, V: np.ndarray, sides: int) -> None:
+    """Open (zero-gradient) ghost fill of the given sides on padded arrays."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    lib().oracle_fill_open(nx, ny, sides, _ptr(H), _ptr(U), _ptr(V))
+
+
+def pad_bed(b: np.ndarray) -> np.ndarray:
+    """Interior bed elevation (ny, nx) -> padded, ghosts copying the edge
+    cells (the rule for walls and open sides alike), corners NaN (unread)."""
+    B = np.pad(np.asarray(b, np.float64), 1, mode="edge")
+    B[[0, 0, -1, -1], [0, -1, 0, -1]] = np.nan
+    return B
+
+
+def step_padded_bathy(H, U, V, B, dx, dy, dt, g):
+    """One step with the bed-slope source on padded arrays (ghosts filled)."""
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    L = lib()
+    out = [np.zeros_like(H) for _ in range(3)]
+    faces = np.zeros(L.oracle_face_workspace(nx, ny), dtype=np.float64)
+    L.oracle_step_bathy(nx, ny, dx, dy, dt, g, _ptr(H), _ptr(U), _ptr(V), _ptr(B),
+                        _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(faces))
+    return out
+
+
+def run_bc(h, hu, hv, dx, dy, dt, g, n_steps, walls=WALL_ALL, open_sides=0, bed=None):
+    """n_steps on interior arrays with reflective ``walls`` sides, open
+    ``open_sides`` (bitmasks left 1, right 2, bottom 4, top 8) and, if
+    ``bed`` (ny, nx) is given, the bed-slope source; returns interiors."""
+    H, U, V = pad(np.asarray(h, np.float64)), pad(np.asarray(hu, np.float64)), pad(np.asarray(hv, np.float64))
+    ny, nx = H.shape[0] - 2, H.shape[1] - 2
+    B = pad_bed(bed) if bed is not None else None
+    rc = lib().oracle_run_bc(nx, ny, walls, open_sides, dx, dy, dt, g, int(n_steps), _ptr(H), _ptr(U), _ptr(V),
+                             _ptr(B) if B is not None else None)
+    if rc != 0:
+        raise MemoryError("oracle_run_bc could not allocate its buffers")
+    return H[1:-1, 1:-1].copy(), U[1:-1, 1:-1].copy(), V[1:-1, 1:-1].copy()
+
+
 def run(h, hu, hv, dx, dy, dt, g, n_steps):
     """n_steps with reflective walls on interior arrays; returns interiors."""
     H, U, V = pad(np.asarray(h, np.float64)), pad(np.asarray(hu, np.float64)), pad(np.asarray(hv, np.float64))
@@ -171,7 +217,8 @@ def cfl_dt(h, hu, hv, dx, dy, g, cfl) -> float:
 
 def run_window(ic: Callable[[Tuple[int, int, int, int]], Tuple[np.ndarray, np.ndarray, np.ndarray]],
                nx: int, ny: int, window: Tuple[int, int, int, int],
-               dx, dy, dt, g, n_steps, binary32: bool = False):
+               dx, dy, dt, g, n_steps, binary32: bool = False, open_sides: int = 0,
+               bed: Callable[[Tuple[int, int, int, int]], np.ndarray] | None = None):
     """Exact values on a window of a large grid after n_steps.
 
     The scheme reads only the four edge neighbours of a cell, so after n
@@ -182,20 +229,41 @@ def run_window(ic: Callable[[Tuple[int, int, int, int]], Tuple[np.ndarray, np.nd
     values on sides that are not walls, and the ordinary step runs on it with
     reflective fill on the wall sides only.  Cells inside ``window`` are then
     exactly those of the full-grid run (checked bitwise in the tests).
-    ``binary32`` runs the binary32 step instead of the FP64 one.
+    ``binary32`` runs the binary32 step instead of the FP64 one.  Sides of
+    the grid named in ``open_sides`` are open instead of walls, and ``bed``
+    (evaluated like ``ic``) runs the step over that bed (FP64 only; its
+    ghosts on the grid boundary copy the edge cells).
     Returns (h, hu, hv) on the window, shape (j1-j0+1, i1-i0+1).
     """
     i0, i1, j0, j1 = window
     n = int(n_steps)
     a, b = max(1, i0 - n + 1), min(nx, i1 + n - 1)
     c, d = max(1, j0 - n + 1), min(ny, j1 + n - 1)
-    walls = 0
-    walls |= WALL_LEFT if a == 1 else 0
-    walls |= WALL_RIGHT if b == nx else 0
-    walls |= WALL_BOTTOM if c == 1 else 0
-    walls |= WALL_TOP if d == ny else 0
+    edges = 0
+    edges |= WALL_LEFT if a == 1 else 0
+    edges |= WALL_RIGHT if b == nx else 0
+    edges |= WALL_BOTTOM if c == 1 else 0
+    edges |= WALL_TOP if d == ny else 0
+    walls, opens = edges & ~open_sides, edges & open_sides
     fields = ic((a - 1, b + 1, c - 1, d + 1))
-    if binary32:
+    if bed is not None or opens:
+        assert not binary32
+        H, U, V = (np.ascontiguousarray(f, dtype=np.float64) for f in fields)
+        B = None
+        if bed is not None:
+            B = np.ascontiguousarray(bed((a - 1, b + 1, c - 1, d + 1)), dtype=np.float64)
+            if edges & WALL_LEFT:
+                B[:, 0] = B[:, 1]
+            if edges & WALL_RIGHT:
+                B[:, -1] = B[:, -2]
+            if edges & WALL_BOTTOM:
+                B[0, :] = B[1, :]
+            if edges & WALL_TOP:
+                B[-1, :] = B[-2, :]
+        if lib().oracle_run_bc(b - a + 1, d - c + 1, walls, opens, dx, dy, dt, g, n, _ptr(H), _ptr(U), _ptr(V),
+                               _ptr(B) if B is not None else None):
+            raise MemoryError("oracle_run_bc could not allocate its buffers")
+    elif binary32:
         H, U, V = (np.ascontiguousarray(f, dtype=np.float32) for f in fields)
         if lib().oracle_run_f32(b - a + 1, d - c + 1, walls, dx, dy, dt, g, n, _ptr32(H), _ptr32(U), _ptr32(V)):
             raise MemoryError("oracle_run_f32 could not allocate its buffers")

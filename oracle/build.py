@@ -14,7 +14,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "swe_oracle.c")
-SRCS = [SRC, os.path.join(HERE, "swe_oracle_f32.c")]
+SRCS = [SRC, os.path.join(HERE, "swe_oracle_f32.c"), os.path.join(HERE, "swe_oracle_bathy.c")]
 LIB = os.path.join(HERE, "_swe_oracle.so")
 
 

@@ -104,6 +104,10 @@ _SIGS = {
     "swe_region_destroy": (None, [_vp]),
     "swe_region_step": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _d, _d, _d, _vp]),
     "swe_region_walls": (_i, [_vp, ctypes.POINTER(_vp), _i, _vp]),
+    "swe_region_step_bed": (_i, [_vp, ctypes.POINTER(_vp), _vp, ctypes.POINTER(_vp), _d, _d, _d, _d, _vp]),
+    "swe_region_boundary": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i), _vp]),
+    "swe_region_run_bc": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _i, ctypes.POINTER(_i), _d, _d, _d,
+                               _d, _vp, ctypes.POINTER(_i)]),
     "swe_region_run": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _d, _d, _d, _d, _vp,
                             ctypes.POINTER(_i)]),
     "swe_region_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
@@ -376,8 +380,12 @@ def swe_region_shapes(nx, ny):
     return [(ext[2 * k], ext[2 * k + 1]) for k in range(min(n.value, 16))]
 
 
+def _addr(p):
+    return int(p.data_ptr()) if hasattr(p, "data_ptr") else int(p)
+
+
 def _ptr3(planes):
-    return (_vp * 3)(*[int(p.data_ptr()) if hasattr(p, "data_ptr") else int(p) for p in planes])
+    return (_vp * 3)(*[_addr(p) for p in planes])
 
 
 class Region:
@@ -425,6 +433,24 @@ class Region:
     def walls(self, state, walls=15, stream=None):
         check(lib().swe_region_walls(self.r, _ptr3(state), int(walls),
                                      stream if stream is not None else current_stream()), "swe_region_walls")
+
+    def step_bed(self, src, bed, dst, dx, dy, dt, g, stream=None):
+        check(lib().swe_region_step_bed(self.r, _ptr3(src), _vp(_addr(bed)), _ptr3(dst), dx, dy, dt, g,
+                                        stream if stream is not None else current_stream()), "swe_region_step_bed")
+
+    def boundary(self, state, kinds, stream=None):
+        """kinds per side (left, right, bottom, top): 0 none, 1 wall, 2 open."""
+        check(lib().swe_region_boundary(self.r, _ptr3(state), (_i * 4)(*kinds),
+                                        stream if stream is not None else current_stream()), "swe_region_boundary")
+
+    def run_bc(self, a, b, n_steps, dx, dy, dt, g, kinds=(1, 1, 1, 1), bed=None, stream=None):
+        """n_steps of (boundary, step[, over the bed]) from a; returns 1 if the result is in b."""
+        in_b = _i()
+        check(lib().swe_region_run_bc(self.r, _ptr3(a), _ptr3(b), _vp(_addr(bed)) if bed is not None else None,
+                                      int(n_steps), (_i * 4)(*kinds), dx, dy, dt, g,
+                                      stream if stream is not None else current_stream(), ctypes.byref(in_b)),
+              "swe_region_run_bc")
+        return in_b.value
 
     def run(self, a, b, n_steps, dx, dy, dt, g, walls=15, stream=None):
         """n_steps of (walls, step) from a; returns 1 if the result is in b."""

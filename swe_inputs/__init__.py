@@ -172,6 +172,21 @@ def large_grid_state(seed: int = 1, n: int = 8192, count: int = 64,
     return _at_rest(h)
 
 
+def large_grid_bed(seed: int = 2, n: int = 8192, count: int = 32, window=None) -> np.ndarray:
+    """Bed elevation of the topography workload: 32 Gaussian mounds on a zero
+    base, amp U[0.02, 0.2], sigma U[16, 128] (well below the still-water
+    surface at 1)."""
+    bumps = multi_bumps(seed, 0xBED, n, n, count, amp_range=(0.02, 0.2), sigma_range=(16.0, 128.0))
+    return bumps_h(n, n, 0.0, bumps, window)
+
+
+def large_grid_bed_state(seed: int = 1, bed_seed: int = 2, n: int = 8192, window=None) -> State:
+    """The default workload's surface (1 + 64 bumps) over the bed of
+    ``large_grid_bed``: depth = surface - bed, at rest."""
+    surface = bumps_h(n, n, 1.0, large_grid_bumps(seed, n), window)
+    return _at_rest(surface - large_grid_bed(bed_seed, n, window=window))
+
+
 def ensemble_sizes(seed: int = 2, count: int = 512, lo: int = 64, hi: int = 1024):
     """Instance sizes (nx, ny), each uniform over the integers [lo, hi]."""
     rng = SplitMix64(seed, 0xE5E)
