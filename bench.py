@@ -119,6 +119,8 @@ def measured_peaks():
 # Sources a step kernel's arithmetic and staging come from (its DRAM traffic
 # is reported only while they are unchanged since the counters were taken).
 KERNEL_SOURCES = {
+    "lw_tb2_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_temporal.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
+                             "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "region_lw_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_region.cu", "paper_1107_2157_gb300/csrc/swe_region.cuh",
                                 "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "region_lw_kernel<float, bed>": ("paper_1107_2157_gb300/csrc/swe_region.cu",

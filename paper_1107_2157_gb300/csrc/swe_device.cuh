@@ -288,4 +288,177 @@ __device__ __forceinline__ void lw_update(T &h, T &u, T &v, const Flux3<T> &Fl, 
     v = fma(k.ly, Gd.c - Gu.c, fma(k.lx, Fl.c - Fr.c, v));
 }
 
+// ---------------------------------------------------------------------------
+// The same arithmetic on two FP32 cells at once.  An F2 holds two floats in
+// one 64-bit register pair; add/sub/mul/fma.rn.f32x2 perform on each lane
+// exactly the IEEE operation the scalar functions above perform, and the
+// reciprocal is taken per lane with the same instruction, so every lane of
+// a paired result has the bits of the scalar computation.  Used by the tile
+// routine for cells away from an x-wall.
+// ---------------------------------------------------------------------------
+struct F2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ F2 pack2(float lo, float hi)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(F2 x, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x.v));
+}
+__device__ __forceinline__ float lo2(F2 x)
+{
+    float a, b;
+    unpack2(x, a, b);
+    return a;
+}
+__device__ __forceinline__ float hi2(F2 x)
+{
+    float a, b;
+    unpack2(x, a, b);
+    return b;
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b)
+{
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ F2 rcp2(F2 x)
+{
+    float a, b;
+    unpack2(x, a, b);
+    return pack2(rcp(a), rcp(b));
+}
+__device__ __forceinline__ F2 neg2(F2 x)  // exact sign flip of both lanes
+{
+    F2 r;
+    r.v = x.v ^ 0x8000000080000000ull;
+    return r;
+}
+
+struct CellQ2 {
+    F2 h, u, v;
+    F2 f2, f3, g3;
+};
+struct Flux2 {
+    F2 a, b, c;
+};
+// the coefficients broadcast to both lanes
+struct Coef2 {
+    F2 hx, hy, lx, ly, hg, half;
+};
+__device__ __forceinline__ Coef2 coef2(const Coef<float> &k)
+{
+    return {pack2(k.hx, k.hx), pack2(k.hy, k.hy), pack2(k.lx, k.lx), pack2(k.ly, k.ly), pack2(k.hg, k.hg),
+            pack2(0.5f, 0.5f)};
+}
+
+// make_cell on two cells
+__device__ __forceinline__ CellQ2 make_cell2(F2 h, F2 u, F2 v, const Coef2 &k)
+{
+    CellQ2 c;
+    c.h = h;
+    c.u = u;
+    c.v = v;
+    const F2 inv = rcp2(h);
+    const F2 p = mul2(mul2(k.hg, h), h);
+    const F2 uu = mul2(u, inv);
+    const F2 vv = mul2(v, inv);
+    c.f2 = fma2(u, uu, p);
+    c.f3 = mul2(u, vv);
+    c.g3 = fma2(v, vv, p);
+    return c;
+}
+
+__device__ __forceinline__ CellQ2 mirror_y2(const CellQ2 &c)
+{
+    CellQ2 m = c;
+    m.v = neg2(c.v);
+    m.f3 = neg2(c.f3);
+    return m;
+}
+
+// two scalar cells as a pair, and back
+__device__ __forceinline__ CellQ2 pair_cells(const CellQ<float> &a, const CellQ<float> &b)
+{
+    return {pack2(a.h, b.h), pack2(a.u, b.u), pack2(a.v, b.v), pack2(a.f2, b.f2), pack2(a.f3, b.f3),
+            pack2(a.g3, b.g3)};
+}
+__device__ __forceinline__ CellQ<float> cell_lo(const CellQ2 &c)
+{
+    return {lo2(c.h), lo2(c.u), lo2(c.v), lo2(c.f2), lo2(c.f3), lo2(c.g3)};
+}
+__device__ __forceinline__ CellQ<float> cell_hi(const CellQ2 &c)
+{
+    return {hi2(c.h), hi2(c.u), hi2(c.v), hi2(c.f2), hi2(c.f3), hi2(c.g3)};
+}
+
+// xface_flux on two faces
+__device__ __forceinline__ Flux2 xface_flux2(const CellQ2 &L, const CellQ2 &R, const Coef2 &k)
+{
+    const F2 Hf = fma2(k.hx, sub2(L.u, R.u), mul2(k.half, add2(L.h, R.h)));
+    const F2 Uf = fma2(k.hx, sub2(L.f2, R.f2), mul2(k.half, add2(L.u, R.u)));
+    const F2 Vf = fma2(k.hx, sub2(L.f3, R.f3), mul2(k.half, add2(L.v, R.v)));
+    const F2 inv = rcp2(Hf);
+    const F2 uf = mul2(Uf, inv);
+    Flux2 F;
+    F.a = Uf;
+    F.b = fma2(Uf, uf, mul2(mul2(k.hg, Hf), Hf));
+    F.c = mul2(Vf, uf);
+    return F;
+}
+
+// yface_flux on two faces
+__device__ __forceinline__ Flux2 yface_flux2(const CellQ2 &D, const CellQ2 &U, const Coef2 &k)
+{
+    const F2 Hf = fma2(k.hy, sub2(D.v, U.v), mul2(k.half, add2(D.h, U.h)));
+    const F2 Uf = fma2(k.hy, sub2(D.f3, U.f3), mul2(k.half, add2(D.u, U.u)));
+    const F2 Vf = fma2(k.hy, sub2(D.g3, U.g3), mul2(k.half, add2(D.v, U.v)));
+    const F2 inv = rcp2(Hf);
+    const F2 vf = mul2(Vf, inv);
+    Flux2 G;
+    G.a = Vf;
+    G.b = mul2(Uf, vf);
+    G.c = fma2(Vf, vf, mul2(mul2(k.hg, Hf), Hf));
+    return G;
+}
+
+// lw_update on two cells
+__device__ __forceinline__ void lw_update2(F2 &h, F2 &u, F2 &v, const Flux2 &Fl, const Flux2 &Fr, const Flux2 &Gd,
+                                           const Flux2 &Gu, const Coef2 &k)
+{
+    h = fma2(k.ly, sub2(Gd.a, Gu.a), fma2(k.lx, sub2(Fl.a, Fr.a), h));
+    u = fma2(k.ly, sub2(Gd.b, Gu.b), fma2(k.lx, sub2(Fl.b, Fr.b), u));
+    v = fma2(k.ly, sub2(Gd.c, Gu.c), fma2(k.lx, sub2(Fl.c, Fr.c), v));
+}
+
+// (lo of a, lo of b) and (hi of a, hi of b) style regroupings of fluxes
+__device__ __forceinline__ Flux2 flux_pair(float a0, float b0, float c0, float a1, float b1, float c1)
+{
+    return {pack2(a0, a1), pack2(b0, b1), pack2(c0, c1)};
+}
+
 }  // namespace swe

@@ -4,6 +4,8 @@
 // the tile's cells (Sec. 3 step equations), storing them to global memory.
 #pragma once
 
+#include <type_traits>
+
 #include "swe_device.cuh"
 
 namespace swe {
@@ -61,6 +63,20 @@ struct SoaBox {
         load_row<T, VX>(h, u, v, idx, hg, c);
     }
     __device__ __forceinline__ CellQ<T> cell(int idx, T hg) const { return make_cell<T>(h[idx], u[idx], v[idx], hg); }
+    // FP32: cells idx .. idx+3 as the pairs (0, 1), (2, 3); and two single
+    // cells a, b as one pair
+    __device__ __forceinline__ void row2(int idx, const Coef2 &k, CellQ2 (&c)[2]) const
+    {
+        const float4 hh = *reinterpret_cast<const float4 *>(h + idx);
+        const float4 uu = *reinterpret_cast<const float4 *>(u + idx);
+        const float4 vv = *reinterpret_cast<const float4 *>(v + idx);
+        c[0] = make_cell2(pack2(hh.x, hh.y), pack2(uu.x, uu.y), pack2(vv.x, vv.y), k);
+        c[1] = make_cell2(pack2(hh.z, hh.w), pack2(uu.z, uu.w), pack2(vv.z, vv.w), k);
+    }
+    __device__ __forceinline__ CellQ2 cell2(int a, int b, const Coef2 &k) const
+    {
+        return make_cell2(pack2(h[a], h[b]), pack2(u[a], u[b]), pack2(v[a], v[b]), k);
+    }
 };
 
 struct PackedBox {
@@ -78,6 +94,17 @@ struct PackedBox {
     {
         const float4 s = p[idx];
         return make_cell<float>(s.x, s.y, s.z, hg);
+    }
+    __device__ __forceinline__ void row2(int idx, const Coef2 &k, CellQ2 (&c)[2]) const
+    {
+        const float4 s0 = p[idx], s1 = p[idx + 1], s2 = p[idx + 2], s3 = p[idx + 3];
+        c[0] = make_cell2(pack2(s0.x, s1.x), pack2(s0.y, s1.y), pack2(s0.z, s1.z), k);
+        c[1] = make_cell2(pack2(s2.x, s3.x), pack2(s2.y, s3.y), pack2(s2.z, s3.z), k);
+    }
+    __device__ __forceinline__ CellQ2 cell2(int a, int b, const Coef2 &k) const
+    {
+        const float4 sa = p[a], sb = p[b];
+        return make_cell2(pack2(sa.x, sb.x), pack2(sa.y, sb.y), pack2(sa.z, sb.z), k);
     }
 };
 
@@ -98,12 +125,81 @@ __device__ __forceinline__ void store_vec(T *dst, const T (&x)[VX])
 // receives each finished row.
 // GHOSTED: the box's halo holds real neighbour cells everywhere (a
 // partition's ghost ring), so no wall is formed; use with XEDGE = false.
+// The FP32, four-cells-per-thread form of strip_compute_box for columns away
+// from an x-wall, on the packed FP32 pipe: the thread's cells form the pairs
+// (0, 1) and (2, 3); its five x-faces are computed as the pairs (F0, F1),
+// (F2, F3) and F4 alone, its four y-faces and updates as two pairs.  Every
+// value goes through the operations of the scalar routine, so the bits are
+// the same.
+template <bool GHOSTED, typename Box, typename Store>
+__device__ __forceinline__ void strip_compute_pairs(const Box &box, int BW, int AX, int row_off, int r_begin,
+                                                    int r_end, int cx, int ny, int y0, const Coef<float> &k,
+                                                    Store &&store)
+{
+    auto sidx = [&](int c, int r) { return (r + row_off) * BW + c + AX; };
+    const Coef2 k2 = coef2(k);
+    CellQ2 cur[2], nxt[2];
+    Flux2 gd[2], gu[2];
+
+    box.row2(sidx(cx, r_begin), k2, cur);
+    if (!GHOSTED && y0 + r_begin == 0) {
+        nxt[0] = mirror_y2(cur[0]);
+        nxt[1] = mirror_y2(cur[1]);
+    } else {
+        box.row2(sidx(cx, r_begin - 1), k2, nxt);
+    }
+    gd[0] = yface_flux2(nxt[0], cur[0], k2);
+    gd[1] = yface_flux2(nxt[1], cur[1], k2);
+
+#pragma unroll 1
+    for (int r = r_begin; r < r_end; ++r) {
+        if (!GHOSTED && y0 + r + 1 == ny) {
+            nxt[0] = mirror_y2(cur[0]);
+            nxt[1] = mirror_y2(cur[1]);
+        } else {
+            box.row2(sidx(cx, r + 1), k2, nxt);
+        }
+        gu[0] = yface_flux2(cur[0], nxt[0], k2);
+        gu[1] = yface_flux2(cur[1], nxt[1], k2);
+
+        // (left, right) neighbours of the thread's four cells on row r
+        const CellQ2 lr = box.cell2(sidx(cx - 1, r), sidx(cx + 4, r), k2);
+        const CellQ<float> c1 = cell_hi(cur[0]), c2 = cell_lo(cur[1]), c3 = cell_hi(cur[1]);
+        const Flux2 F01 = xface_flux2(pair_cells(cell_lo(lr), cell_lo(cur[0])), cur[0], k2);
+        const Flux2 F23 = xface_flux2(pair_cells(c1, c2), cur[1], k2);
+        const Flux3<float> F4 = xface_flux(c3, cell_hi(lr), k);
+        const Flux2 F12 = flux_pair(hi2(F01.a), hi2(F01.b), hi2(F01.c), lo2(F23.a), lo2(F23.b), lo2(F23.c));
+        const Flux2 F34 = flux_pair(hi2(F23.a), hi2(F23.b), hi2(F23.c), F4.a, F4.b, F4.c);
+
+        F2 oh0 = cur[0].h, ou0 = cur[0].u, ov0 = cur[0].v;
+        F2 oh1 = cur[1].h, ou1 = cur[1].u, ov1 = cur[1].v;
+        lw_update2(oh0, ou0, ov0, F01, F12, gd[0], gu[0], k2);
+        lw_update2(oh1, ou1, ov1, F23, F34, gd[1], gu[1], k2);
+        float oh[4], ou[4], ov[4];
+        unpack2(oh0, oh[0], oh[1]);
+        unpack2(oh1, oh[2], oh[3]);
+        unpack2(ou0, ou[0], ou[1]);
+        unpack2(ou1, ou[2], ou[3]);
+        unpack2(ov0, ov[0], ov[1]);
+        unpack2(ov1, ov[2], ov[3]);
+        store(r, oh, ou, ov);
+        cur[0] = nxt[0];
+        cur[1] = nxt[1];
+        gd[0] = gu[0];
+        gd[1] = gu[1];
+    }
+}
+
 template <typename T, int VX, bool XEDGE, typename Box, typename Store, bool GHOSTED = false>
 __device__ __forceinline__ void strip_compute_box(const Box &box, int BW, int AX, int row_off, int r_begin, int r_end,
                                                   int cx, int gx, int nx, int ny, int y0, const Coef<T> &k,
                                                   Store &&store)
 {
     if (r_begin >= r_end) return;
+    if constexpr (std::is_same<T, float>::value && VX == 4 && !XEDGE) {
+        strip_compute_pairs<GHOSTED>(box, BW, AX, row_off, r_begin, r_end, cx, ny, y0, k, store);
+        return;
+    }
     auto sidx = [&](int c, int r) { return (r + row_off) * BW + c + AX; };
     const int pw = nx - gx;  // window position of the right wall ghost, if in 1..VX
 

@@ -334,3 +334,24 @@ def test_packed_kernel_reductions_and_fp64_rejection():
     with pytest.raises(swe.SweError) as e:
         Grid(16, 16, 1.0, 1.0, 0.01, G, dtype="f64", kernel=4)
     assert e.value.status == swe.SWE_EUNSUPPORTED
+
+
+def test_auto_picks_the_two_step_kernel_for_fp32_and_the_one_step_kernel_for_fp64():
+    from paper_1107_2157_gb300 import Grid, swe
+    with Grid(64, 64, 1.0, 1.0, 0.01, G, dtype="f32") as g:
+        assert g.query(swe.SWE_Q_KERNEL) == 3 and g.query(swe.SWE_Q_STEPS_PER_LAUNCH) == 2
+    with Grid(64, 64, 1.0, 1.0, 0.01, G, dtype="f64") as g:
+        assert g.query(swe.SWE_Q_KERNEL) == 2 and g.query(swe.SWE_Q_STEPS_PER_LAUNCH) == 1
+
+
+@pytest.mark.parametrize("nx,ny", [(1024, 96), (517, 263)])
+def test_paired_interior_tiles_equal_the_scalar_naive_kernel(nx, ny):
+    """Tiles away from an x-wall take the FP32 pair path (f32x2 arithmetic),
+    tiles at a wall and the naive kernel the scalar one: same bits."""
+    s = si.smooth_flow_state(nx + ny, nx, ny).rounded_to(np.float32)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.3)
+    ref = run_gpu(s, 1.0, 1.0, dt, G, 9, "f32", KERNELS["naive"])
+    for kernel in (KERNELS["tiled"], 3, 4):
+        got = run_gpu(s, 1.0, 1.0, dt, G, 9, "f32", kernel)
+        for k in range(3):
+            assert np.array_equal(got[k], ref[k]), (kernel, k)
