@@ -47,6 +47,9 @@
 #ifndef SWE_LEARN_NG
 #define SWE_LEARN_NG 2
 #endif
+#ifndef SWE_LEARN_C0
+#define SWE_LEARN_C0 8
+#endif
 
 namespace swe {
 
@@ -64,7 +67,11 @@ struct LearnCfg {
     static constexpr int RING = 2, LW_SLOTS = 7;
     static constexpr int NCW = 4 * NH * NG;  // compute warps; one more issues the MMAs
     static constexpr int THREADS = (NCW + 1) * 32;
-    static constexpr int CPT = 32 / NG;      // hidden channels per epilogue thread
+    // hidden channels per epilogue thread: group 0 (which also runs the
+    // Lax-Wendroff row and the output stage) takes C0, group 1 the rest
+    static constexpr int C0 = NG == 1 ? 32 : SWE_LEARN_C0;
+    static constexpr int C1 = 32 - C0;
+    static_assert(C0 % 8 == 0 && C0 >= 0 && C0 <= 32 && (NG == 2 || C0 == 32), "hidden channel split in 8-channel strips");
     // Weight images: per layer, rotation rho (0..2), kx, K step s, a 16 x 3C
     // K-major B operand [K core 2][N core 3C/8][8 x 16 B].
     static constexpr size_t IMG1 = 2 * 12 * 128, IMG2 = 2 * 12 * 128, IMG3 = 2 * 6 * 128;
@@ -164,15 +171,39 @@ __device__ __forceinline__ void load16(const float *p, float (&b)[16])
     }
 }
 
-// Arms CPT accumulator columns at taddr with the bias (TMEM store).
+// Arms CPT accumulator columns at taddr with the bias (TMEM store); an odd
+// 8 columns first, so that every 16-column store starts on a multiple of 16
+// when taddr's column is a multiple of 16 or sits 8 past one.
 template <int CPT>
 __device__ __forceinline__ void arm(uint32_t taddr, const float *bias)
 {
+    static_assert(CPT % 8 == 0, "8-column granules");
+    constexpr int LEAD = CPT % 16;
+    if constexpr (LEAD == 8) {
+        float b[16];
+        load16(bias, b);  // 16 floats are readable: the bias block has 80
+        tc::st_x8(taddr, b);
+    }
 #pragma unroll
     for (int c = 0; c < CPT / 16; ++c) {
         float b[16];
-        load16(bias + 16 * c, b);
-        tc::st_x16(taddr + 16 * c, b);
+        load16(bias + LEAD + 16 * c, b);
+        tc::st_x16(taddr + LEAD + 16 * c, b);
+    }
+}
+
+// CPT accumulator columns at taddr into v, in the same granules as arm.
+template <int CPT>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[CPT])
+{
+    constexpr int LEAD = CPT % 16;
+    if constexpr (LEAD == 8) tc::ld_x8(taddr, v);
+#pragma unroll
+    for (int c = 0; c < CPT / 16; ++c) {
+        float w[16];
+        tc::ld_x16(taddr + LEAD + 16 * c, w);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[LEAD + 16 * c + i] = w[i];
     }
 }
 
@@ -185,10 +216,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bia
                                                 bool valid)
 {
     float v[CPT];
-    if constexpr (CPT == 32)
-        tc::ld_x32(taddr, v);
-    else
-        tc::ld_x16(taddr, v);
+    tmem_load<CPT>(taddr, v);
     arm<CPT>(taddr, bias);
 #pragma unroll
     for (int c = 0; c < CPT / 8; ++c) {
@@ -365,10 +393,26 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
         const bool lw_thread = g == 0;
         const uint32_t tl = (uint32_t)(32 * q) << 16;
         // this thread's accumulator columns (block 0) of each layer
-        const uint32_t t1 = tmem + tl + C::ACC1 + hh * 96 + C::CPT * g;
-        const uint32_t t2 = tmem + tl + C::ACC2 + hh * 96 + C::CPT * g;
+        const int ch = g == 0 ? 0 : C::C0;  // this thread's first hidden channel
+        const uint32_t t1 = tmem + tl + C::ACC1 + hh * 96 + ch;
+        const uint32_t t2 = tmem + tl + C::ACC2 + hh * 96 + ch;
         const uint32_t t3 = tmem + tl + C::ACC3 + hh * 48;
-        const int sw = (C::CPT / 8) * g * C::STRIP + (px + 1) * 16;  // ring offset of this thread's strips
+        const int sw = (ch / 8) * C::STRIP + (px + 1) * 16;  // ring offset of this thread's strips
+        // the hidden-layer epilogue with this group's channel count
+        auto epilogue = [&](uint32_t taddr, const float *bias, unsigned char *dst, bool valid) {
+            if (g == 0) {
+                if constexpr (C::C0 > 0) hidden_epilogue<C::C0>(taddr, bias, dst, C::STRIP, valid);
+            } else {
+                if constexpr (C::C1 > 0) hidden_epilogue<C::C1>(taddr, bias, dst, C::STRIP, valid);
+            }
+        };
+        auto arm_hidden = [&](uint32_t taddr, const float *bias) {
+            if (g == 0) {
+                if constexpr (C::C0 > 0) arm<C::C0>(taddr, bias);
+            } else {
+                if constexpr (C::C1 > 0) arm<C::C1>(taddr, bias);
+            }
+        };
         uint32_t nb = 0;  // batches of the finished sweeps
         // waits for ``bar`` (per thread); records a give-up for everyone
         auto wait = [&](uint64_t *bar, uint32_t par) {
@@ -413,8 +457,8 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                 // for them)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    arm<C::CPT>(t1 + b * 32, sBias + C::CPT * g);
-                    arm<C::CPT>(t2 + b * 32, sBias + 32 + C::CPT * g);
+                    arm_hidden(t1 + b * 32, sBias + ch);
+                    arm_hidden(t2 + b * 32, sBias + 32 + ch);
                     if (lw_thread) arm<16>(t3 + b * 16, sBias + 64);
                 }
                 double hs = 0.0;
@@ -477,15 +521,13 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                     if (t >= 1) wait(bars + B_L1, parW);
                     const int r1 = t - 2;
                     if (r1 >= 0 && r1 < H)
-                        hidden_epilogue<C::CPT>(t1 + mod3(r1) * 32, sBias + C::CPT * g, sA1 + (r1 & 1) * C::A_ROW + sw,
-                                                C::STRIP, inside);
+                        epilogue(t1 + mod3(r1) * 32, sBias + ch, sA1 + (r1 & 1) * C::A_ROW + sw, inside);
                     if (publish_t) publish(bars + B_RDY1, lane);
                     // ---- E2 of row t-4 ----
                     if (t >= 1) wait(bars + B_L2, parW);
                     const int r2 = t - 4;
                     if (r2 >= 0 && r2 < H)
-                        hidden_epilogue<C::CPT>(t2 + mod3(r2) * 32, sBias + 32 + C::CPT * g,
-                                                sA2 + (r2 & 1) * C::A_ROW + sw, C::STRIP, inside);
+                        epilogue(t2 + mod3(r2) * 32, sBias + 32 + ch, sA2 + (r2 & 1) * C::A_ROW + sw, inside);
                     if (publish_t) publish(bars + B_RDY2, lane);
                     // ---- E3: corrected row t-6 ----
                     if (t >= 1) wait(bars + B_L3, parW);
