@@ -395,7 +395,7 @@ swe_status swe_region_query(swe_region *r, int key, long long *value);
  * the step and the wall fill take on nx x ny interior cells, in order:
  * cell fluxes, x-faces, y-faces, update, then the left, right, bottom and top ghost
  * strips.  ext receives 2 * min(*n_groups, max_groups) ints; an extent of a
- * group whose regions do not conform is negative. */
+ * group whose regions do not conform is negative.  1 <= nx, ny <= 65536. */
 swe_status swe_region_shapes(int nx, int ny, int *ext, int max_groups, int *n_groups);
 /* Self-test of the FP32 division of the region statements: out[i] =
  * a[i] / b[i] correctly rounded, by the statements' FMA division (which = 0)

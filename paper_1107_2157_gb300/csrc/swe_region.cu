@@ -16,7 +16,6 @@
 #include <cmath>
 #include <mutex>
 #include <new>
-#include <vector>
 
 #include "swe_device.cuh"
 #include "swe_region.cuh"
@@ -616,13 +615,8 @@ swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, i
 
 swe_status swe_region_shapes(int nx, int ny, int *ext, int max_groups, int *n_groups)
 {
-    if (!ext || !n_groups || nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || max_groups < 0) return SWE_EINVAL;
-    // Nothing is evaluated: the arrays only need addresses inside one buffer.
-    std::vector<double> buf((size_t)(nx + 2) * (size_t)(ny + 2));
-    double *p = buf.data();
-    const Array<double> C = array(p, nx + 2, ny + 2, (long long)nx + 2);
-    const Array<double> X = array(p, nx + 1, ny, (long long)nx + 1);
-    const Array<double> Y = array(p, nx, ny + 1, (long long)nx);
+    if (!ext || !n_groups || nx < 1 || ny < 1 || nx > 65536 || ny > 65536 || max_groups < 0) return SWE_EINVAL;
+    const ShapeArray<double> C{nx + 2, ny + 2}, X{nx + 1, ny}, Y{nx, ny + 1};
     ShapeRun run;
     lw_statements<double>(run, C, C, C, C, C, C, X, X, X, Y, Y, Y, C, C, C, lw_coef<double>(1.0, 1.0, 0.1, 9.8));
     boundary_statements(run, C, C, C, sides_of_walls(15));

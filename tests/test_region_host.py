@@ -15,7 +15,7 @@ def _lib():
     return swe
 
 
-@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (10, 7), (64, 8), (129, 33), (4096, 3)])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (10, 7), (64, 8), (129, 33), (4096, 3), (65536, 65536)])
 def test_statement_extents(nx, ny):
     ext = _lib().swe_region_shapes(nx, ny)
     assert ext == [(nx + 2, ny + 2),                          # cell fluxes
@@ -37,7 +37,7 @@ def test_shapes_rejects_bad_sizes():
     swe = _lib()
     ext = (ctypes.c_int * 32)()
     n = ctypes.c_int()
-    for nx, ny in [(0, 5), (5, 0), (5000, 5), (-1, -1)]:
+    for nx, ny in [(0, 5), (5, 0), (70000, 5), (-1, -1)]:
         assert swe.lib().swe_region_shapes(nx, ny, ext, 16, ctypes.byref(n)) == swe.SWE_EINVAL
 
 
