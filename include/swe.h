@@ -398,8 +398,10 @@ swe_status swe_region_query(swe_region *r, int key, long long *value);
  * group whose regions do not conform is negative.  1 <= nx, ny <= 65536. */
 swe_status swe_region_shapes(int nx, int ny, int *ext, int max_groups, int *n_groups);
 /* Self-test of the FP32 division of the region statements: out[i] =
- * a[i] / b[i] correctly rounded, by the statements' FMA division (which = 0)
- * or by CUDA's __fdiv_rn (1); device pointers, n >= 0; stream-ordered. */
+ * a[i] / b[i] correctly rounded, by the statements' FMA division (which = 0),
+ * by the same division on element pairs (2m, 2m + 1) as the paired FP32
+ * evaluation takes it (2; n even), or by CUDA's __fdiv_rn (1); device
+ * pointers, n >= 0; stream-ordered. */
 swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, int which, void *stream);
 
 /* ==========================================================================

@@ -293,7 +293,8 @@ __device__ __forceinline__ void lw_update(T &h, T &u, T &v, const Flux3<T> &Fl, 
 // one 64-bit register pair; add/sub/mul/fma.rn.f32x2 perform on each lane
 // exactly the IEEE operation the scalar functions above perform, and the
 // reciprocal is taken per lane with the same instruction, so every lane of
-// a paired result has the bits of the scalar computation.  Used by the tile
+// a paired result has the bits of the scalar computation, provided no packed
+// product feeds a packed add or subtract (see mul2_rn).  Used by the tile
 // routine for cells away from an x-wall.
 // ---------------------------------------------------------------------------
 struct F2 {
@@ -346,6 +347,18 @@ __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
     return r;
 }
+// A product that a later add or subtract may not absorb.  Unlike the scalar
+// mul.rn, a packed mul.rn.f32x2 whose result feeds an add/sub.rn.f32x2 is
+// fused into one FMA by the compiler (measured on sm_103a, --fmad=false or
+// not), which changes the rounding; two scalar __fmul_rn are not.  Every
+// product that feeds a sum goes through this.
+__device__ __forceinline__ F2 mul2_rn(F2 a, F2 b)
+{
+    float a0, a1, b0, b1;
+    unpack2(a, a0, a1);
+    unpack2(b, b0, b1);
+    return pack2(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
+}
 __device__ __forceinline__ F2 rcp2(F2 x)
 {
     float a, b;
@@ -388,7 +401,7 @@ __device__ __forceinline__ CellQ2 make_cell2(F2 h, F2 u, F2 v, const Coef2 &k)
     const F2 uu = mul2(u, inv);
     const F2 vv = mul2(v, inv);
     c.f2 = fma2(u, uu, p);
-    c.f3 = mul2(u, vv);
+    c.f3 = mul2_rn(u, vv);  // differenced by the face steps
     c.g3 = fma2(v, vv, p);
     return c;
 }
@@ -427,7 +440,7 @@ __device__ __forceinline__ Flux2 xface_flux2(const CellQ2 &L, const CellQ2 &R, c
     Flux2 F;
     F.a = Uf;
     F.b = fma2(Uf, uf, mul2(mul2(k.hg, Hf), Hf));
-    F.c = mul2(Vf, uf);
+    F.c = mul2_rn(Vf, uf);  // differenced by the update
     return F;
 }
 
@@ -441,7 +454,7 @@ __device__ __forceinline__ Flux2 yface_flux2(const CellQ2 &D, const CellQ2 &U, c
     const F2 vf = mul2(Vf, inv);
     Flux2 G;
     G.a = Vf;
-    G.b = mul2(Uf, vf);
+    G.b = mul2_rn(Uf, vf);  // differenced by the update
     G.c = fma2(Vf, vf, mul2(mul2(k.hg, Hf), Hf));
     return G;
 }

@@ -305,6 +305,15 @@ __global__ void __launch_bounds__(S::NT) region_lw_kernel(const __grid_constant_
 
 __global__ void div_probe_kernel(const float *a, const float *b, float *out, int n, int which)
 {
+    if (which == 2) {  // elements 2m, 2m + 1 as one pair (n even)
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; 2 * m < n; m += gridDim.x * blockDim.x) {
+            F2 q;
+            if (!fdiv_fast2(pack2(a[2 * m], a[2 * m + 1]), pack2(b[2 * m], b[2 * m + 1]), q))
+                q = pack2(__fdiv_rn(a[2 * m], b[2 * m]), __fdiv_rn(a[2 * m + 1], b[2 * m + 1]));
+            unpack2(q, out[2 * m], out[2 * m + 1]);
+        }
+        return;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         out[i] = which == 0 ? fdiv_rn(a[i], b[i]) : __fdiv_rn(a[i], b[i]);
 }
@@ -606,7 +615,7 @@ swe_status swe_region_query(swe_region *r, int key, long long *value)
 
 swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, int which, void *stream)
 {
-    if (!a || !b || !out || n < 0 || which < 0 || which > 1) return SWE_EINVAL;
+    if (!a || !b || !out || n < 0 || which < 0 || which > 2 || (which == 2 && n % 2)) return SWE_EINVAL;
     if (n == 0) return SWE_OK;
     div_probe_kernel<<<std::min((n + 255) / 256, 4096), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, b, out, n,
                                                                                                        which);

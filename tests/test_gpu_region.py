@@ -275,23 +275,28 @@ def _div_cases(seed):
 
 
 def test_fp32_division_is_correctly_rounded():
-    """The statements' FP32 division (FMA scheme with an exact rounding test)
-    against CUDA's __fdiv_rn and the host's IEEE division, bit for bit."""
+    """The statements' FP32 division (FMA scheme with an exact rounding test),
+    alone and on element pairs as the paired evaluation takes it, against
+    CUDA's __fdiv_rn and the host's IEEE division, bit for bit."""
     import torch
     from paper_1107_2157_gb300 import swe
     ab = _div_cases(5)
     n = ab.shape[1]
     a, b = (torch.from_numpy(np.ascontiguousarray(ab[k])).cuda() for k in range(2))
+    if n % 2:
+        ab = ab[:, :-1]
+        n -= 1
+        a, b = a[:n], b[:n]
     outs = []
-    for which in (0, 1):
+    for which in (0, 1, 2):
         o = torch.empty_like(a)
         swe.check(swe.lib().swe_selftest_div(a.data_ptr(), b.data_ptr(), o.data_ptr(), n, which,
                                              swe.current_stream()), "swe_selftest_div")
         outs.append(o.cpu().numpy())
     with np.errstate(all="ignore"):
         host = ab[0] / ab[1]
-    mine, cuda = outs
+    mine, cuda, paired = outs
     nan = np.isnan(host)
-    assert np.array_equal(np.isnan(mine), nan) and np.array_equal(np.isnan(cuda), nan)
-    assert np.array_equal(mine[~nan].view(np.uint32), host[~nan].view(np.uint32))
-    assert np.array_equal(cuda[~nan].view(np.uint32), host[~nan].view(np.uint32))
+    for got in (mine, cuda, paired):
+        assert np.array_equal(np.isnan(got), nan)
+        assert np.array_equal(got[~nan].view(np.uint32), host[~nan].view(np.uint32))
