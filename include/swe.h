@@ -46,7 +46,7 @@ typedef enum {
     SWE_ECUDA = 3,        /* a CUDA runtime call failed */
     SWE_ETIMEOUT = 4,     /* a device-side bounded wait gave up */
     SWE_ECHECK = 5,       /* a mass/positivity check failed */
-    SWE_EUNSUPPORTED = 6  /* valid request this build does not support */
+    SWE_EUNSUPPORTED = 6  /* valid request that the library does not support */
 } swe_status;
 
 typedef enum { SWE_F32 = 0, SWE_F64 = 1 } swe_dtype;

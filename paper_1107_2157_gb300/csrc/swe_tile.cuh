@@ -295,6 +295,33 @@ __device__ __forceinline__ void box_cell(const T *sH, const T *sU, const T *sV, 
     lw_update(h, hu, hv, Fl, Fr, Gd, Gu, k);
 }
 
+// Which cells of a tile a thread computes.  A warp normally spans the tile's
+// TX columns, VX cells per lane.  When the grid ends within TX/2 (TX/4)
+// columns of the tile's left edge -- the last column strip of a grid whose
+// width is not a multiple of TX -- the warp is cut into G = 2 (4) lane groups
+// of TX/G columns that take different rows, so such a tile costs 1/G of the
+// row iterations of a full one.  The rows [r0, r1) are cut into NWARP * G
+// runs of (nearly) equal length, one per lane group: RY rows per warp for a
+// full tile, fewer per warp for a tile cut short by the grid's last row.
+// The cell arithmetic does not depend on which thread runs it, so the bits
+// do not either.
+struct TileWork {
+    int cx;      // first tile column of the thread's VX cells
+    int rb, re;  // its tile rows [rb, re)
+};
+
+template <int TX, int VX, int NWARP>
+__device__ __forceinline__ TileWork tile_work(bool xedge, int x0, int nx, int r0, int r1)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = nx - x0;  // grid columns from the tile's left edge on
+    const int G = !xedge ? 1 : (w <= TX / 4 ? 4 : (w <= TX / 2 ? 2 : 1));
+    const int L = 32 / G;                   // lanes per group
+    const int j = warp * G + lane / L;      // the group's index in the CTA
+    const int n = max(r1 - r0, 0), W = NWARP * G;
+    return TileWork{(lane % L) * VX, r0 + j * n / W, r0 + (j + 1) * n / W};
+}
+
 // Computes one output tile from the staged box (see TiledCfg; the box's
 // first row is tile row -ROW_OFF) and stores it.  Returns true if some
 // stored depth is not positive (h <= 0 or NaN).
@@ -305,12 +332,11 @@ __device__ __forceinline__ bool tiled_compute(const T *sH, const T *sU, const T 
 {
     using C = TiledCfg<T, NWARP, RY>;
     constexpr int VX = C::VX;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int cx = lane * VX;
+    const TileWork tw = tile_work<C::TX, VX, NWARP>(XEDGE, x0, nx, 0, min(C::TY, ny - y0));
+    const int cx = tw.cx;
     const int gx = x0 + cx;
-    const int rb = warp * RY;
-    const int re = min(rb + RY, ny - y0);
+    const int rb = tw.rb;
+    const int re = tw.re;
     bool bad = false;
     auto store_fn = [&](int r, const T(&oh)[VX], const T(&ou)[VX], const T(&ov)[VX]) {
         if (gx < nx) {
@@ -353,17 +379,15 @@ __device__ __forceinline__ bool tb2_tile_compute(const T *iH, const T *iU, const
 {
     using C = TiledCfg<T, NWARP, RY>;
     constexpr int VX = C::VX;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cx = lane * VX, gx = x0 + cx, rb = warp * RY;
     const bool xedge = (x0 == 0) || (x0 + C::TX >= nx);
 
-    // phase 1: intermediate state on rows [-1, TY] of the tile's columns; the
-    // first and last warp also take the ring rows -1 and TY
+    // phase 1: intermediate state on rows [-1, TY] of the tile's columns (the
+    // ring rows included), cut among the lane groups as phase 2 cuts them, so
+    // phase 2 finds every cell inside the grid that it reads here or in the
+    // ring columns
     {
-        int r0 = warp == 0 ? -1 : rb;
-        int r1 = warp == NWARP - 1 ? rb + RY + 1 : rb + RY;
-        r0 = max(r0, -y0);
-        r1 = min(r1, ny - y0);
+        const TileWork tw = tile_work<C::TX, VX, NWARP>(xedge, x0, nx, max(-1, -y0), min(C::TY + 1, ny - y0));
+        const int cx = tw.cx, gx = x0 + cx, r0 = tw.rb, r1 = tw.re;
         auto to_mid = [&](int r, const T(&h)[VX], const T(&u)[VX], const T(&v)[VX]) {
             const int o = (r + 1) * C::BW + cx + C::AX;
             store_vec<T, VX>(mH_ + o, h);

@@ -1,7 +1,7 @@
 """Helpers shared by the parity tests: run the GPU library and the oracle on
 the same seeded inputs and compare them field by field.
 
-Relative error of a field (the reading stated in the design doc): max|gpu - ref|
+Relative error of a field (the reading this suite takes of "relative"): max|gpu - ref|
 divided by the field's scale -- max|ref| for h; for the momenta hu, hv the
 larger of max|ref| and the wave momentum h_max * sqrt(g * h_max).  Momenta
 can be identically zero (a state at rest) and, in FP32, their rounding

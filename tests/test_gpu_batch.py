@@ -171,3 +171,33 @@ def test_graph_replay_is_used_and_repeatable():
     for i in range(len(sizes)):
         assert all(np.array_equal(x, y) for x, y in zip(a[i], c[i]))
     print("graph capture in use:", graph)
+
+
+def test_narrow_last_column_strips_equal_the_naive_kernel():
+    """Instances whose last 128-wide column strip holds 1, 32, 33, 64 or 65
+    cells (half- and quarter-warp tiles) and whose last tile row is short:
+    every variant gives the bits of the naive single-grid kernel."""
+    from paper_1107_2157_gb300 import Grid, swe
+    sizes = [(129, 45), (160, 33), (161, 70), (192, 17), (193, 100), (32, 31), (33, 9), (64, 65), (65, 130)]
+    states = _states(sizes, seed=11)
+    dxs, dys = np.ones(len(sizes)), np.ones(len(sizes))
+    dts = _dts(states, dxs, dys)
+    steps = 9
+    refs = []
+    for i, s in enumerate(states):
+        with Grid(sizes[i][0], sizes[i][1], 1.0, 1.0, dts[i], G, dtype="f32", kernel=swe.SWE_KERNEL_NAIVE) as g:
+            g.set_state(*(a.astype(np.float32) for a in (s.h, s.hu, s.hv)))
+            g.step(steps)
+            refs.append(g.get_state())
+    with _make_batch(sizes, states, dxs, dys, dts) as b:
+        for v in range(b.query(swe.SWE_BQ_VARIANT_COUNT)):
+            b.configure(v, 2)
+            for i, s in enumerate(states):
+                b.set_state(i, *(a.astype(np.float32) for a in (s.h, s.hu, s.hv)))
+            b.step(steps)
+            rc, flags = b.status()
+            assert rc == 0 and not flags.any()
+            for i in range(len(sizes)):
+                got = b.get_state(i)
+                for k in range(3):
+                    assert np.array_equal(got[k], refs[i][k]), (v, sizes[i], k)

@@ -355,3 +355,27 @@ def test_paired_interior_tiles_equal_the_scalar_naive_kernel(nx, ny):
         got = run_gpu(s, 1.0, 1.0, dt, G, 9, "f32", kernel)
         for k in range(3):
             assert np.array_equal(got[k], ref[k]), (kernel, k)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_narrow_edge_tiles_equal_the_naive_kernel(dtype):
+    """A tile that the grid's right side cuts within half (a quarter) of the
+    tile width is computed by half- (quarter-) warps working on different
+    rows, and the rows of a tile cut short by the top side are shared evenly
+    among the warps.  Widths on both sides of each cut and ragged heights give
+    the bits of the naive kernel (one thread per cell, no tiles)."""
+    tx = 128 if dtype == "f32" else 64
+    widths = [1, tx // 4, tx // 4 + 1, tx // 2, tx // 2 + 1, tx - 1, tx + tx // 4, tx + tx // 4 + 1,
+              tx + tx // 2, tx + tx // 2 + 1, 2 * tx - 1]
+    kernels = (KERNELS["tiled"], 3) + ((4,) if dtype == "f32" else ())
+    for i, nx in enumerate(widths):
+        ny = 5 + 13 * i
+        s = si.smooth_flow_state(700 + i, nx, ny)
+        if dtype == "f32":
+            s = s.rounded_to(np.float32)
+        dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.3)
+        ref = run_gpu(s, 1.0, 1.0, dt, G, 7, dtype, KERNELS["naive"])
+        for kernel in kernels:
+            got = run_gpu(s, 1.0, 1.0, dt, G, 7, dtype, kernel)
+            for k in range(3):
+                assert np.array_equal(got[k], ref[k]), (nx, ny, kernel, k)
