@@ -92,8 +92,9 @@ __host__ __device__ __forceinline__ void lw_statements(Run &run, const A &H, con
         const auto Hf = 0.5 * (region_cpy(H, lt) + region_cpy(H, rt)) + k.hx * (region_cpy(U, lt) - region_cpy(U, rt));
         const auto Uf = 0.5 * (region_cpy(U, lt) + region_cpy(U, rt)) + k.hx * (region_cpy(Fu, lt) - region_cpy(Fu, rt));
         const auto Vf = 0.5 * (region_cpy(V, lt) + region_cpy(V, rt)) + k.hx * (region_cpy(Fuv, lt) - region_cpy(Fuv, rt));
-        run(region_ptr(Ux, whole) = Uf, region_ptr(FXu, whole) = flux_x_u(Hf, Uf, k.g),
-            region_ptr(FXv, whole) = flux_x_v(Hf, Uf, Vf));
+        // the y-face group reads neither of these: no barrier in between
+        run.independent(region_ptr(Ux, whole) = Uf, region_ptr(FXu, whole) = flux_x_u(Hf, Uf, k.g),
+                        region_ptr(FXv, whole) = flux_x_v(Hf, Uf, Vf));
     }
     // Step 1, y-faces with G and dt / 2dy.
     {
@@ -147,8 +148,8 @@ __host__ __device__ __forceinline__ void bed_statements(Run &run, const A &H, co
         const auto Uf = 0.5 * (region_cpy(U, lt) + region_cpy(U, rt)) + k.hx * (region_cpy(Fu, lt) - region_cpy(Fu, rt)) +
                         k.hx * (k.g * (0.5 * (Hl + Hr)) * (region_cpy(B, lt) - region_cpy(B, rt)));
         const auto Vf = 0.5 * (region_cpy(V, lt) + region_cpy(V, rt)) + k.hx * (region_cpy(Fuv, lt) - region_cpy(Fuv, rt));
-        run(region_ptr(Hx, whole) = Hf, region_ptr(Ux, whole) = Uf, region_ptr(FXu, whole) = flux_x_u(Hf, Uf, k.g),
-            region_ptr(FXv, whole) = flux_x_v(Hf, Uf, Vf));
+        run.independent(region_ptr(Hx, whole) = Hf, region_ptr(Ux, whole) = Uf,
+                        region_ptr(FXu, whole) = flux_x_u(Hf, Uf, k.g), region_ptr(FXv, whole) = flux_x_v(Hf, Uf, Vf));
     }
     {
         const auto Hd = region_cpy(H, dn), Hu = region_cpy(H, up);

@@ -247,8 +247,9 @@ def test_full_size_fp32_region_run_sampled_windows():
 
 def _div_cases(seed):
     """Operand pairs for the division test: random bit patterns (every class:
-    zeros, subnormals, infinities, NaNs), random magnitudes across the range
-    the statements' fast path takes, near-midpoint quotients (a = RN(b m)
+    zeros, subnormals, infinities, NaNs), random magnitudes across the
+    binary32 range and across the statements' fast-path range and its
+    edges, near-midpoint quotients (a = RN(b m)
     for m halfway between two floats: the hardest rounding decisions), and
     special values against each other."""
     rng = np.random.default_rng(seed)
@@ -256,6 +257,10 @@ def _div_cases(seed):
     out = []
     out.append(rng.integers(0, 2 ** 32, size=(2, n), dtype=np.uint64).astype(np.uint32).view(np.float32))
     e = rng.integers(-110, 128, size=(2, n))
+    m = rng.uniform(1.0, 2.0, size=(2, n)) * rng.choice([-1.0, 1.0], size=(2, n))
+    out.append(np.ldexp(m, e).astype(np.float32))
+    # inside the fast path's range (2^-100 <= |a| < 2^100, 2^-20 <= |b| < 2^20) and just outside it
+    e = np.stack([rng.integers(-101, 101, n), rng.integers(-21, 21, n)])
     m = rng.uniform(1.0, 2.0, size=(2, n)) * rng.choice([-1.0, 1.0], size=(2, n))
     out.append(np.ldexp(m, e).astype(np.float32))
     b = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-30, 30, n)).astype(np.float32)
@@ -268,7 +273,11 @@ def _div_cases(seed):
     ones = np.uint32(0x3FFFFFFF) + (np.arange(64, dtype=np.uint32) << 23)  # significand all ones, many binades
     sp = np.concatenate([np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 2.0, 0.5, 3.0,
                                    np.finfo(np.float32).max, np.finfo(np.float32).tiny, 1e-45, 1e-40, 2.0 ** -100,
-                                   2.0 ** -101, 2.0 ** 126, 2.0 ** 127], np.float32), ones.view(np.float32)])
+                                   2.0 ** -101, 2.0 ** 126, 2.0 ** 127, 2.0 ** -20, 2.0 ** 20, 2.0 ** 100,
+                                   np.nextafter(np.float32(2.0 ** -20), np.float32(0)),
+                                   np.nextafter(np.float32(2.0 ** 20), np.float32(0)),
+                                   np.nextafter(np.float32(2.0 ** 100), np.float32(0))], np.float32),
+                         ones.view(np.float32)])
     A, B = np.meshgrid(sp, sp)
     out.append(np.stack([A.ravel(), B.ravel()]))
     return np.concatenate(out, axis=1).astype(np.float32)
