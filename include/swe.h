@@ -400,7 +400,10 @@ swe_status swe_region_shapes(int nx, int ny, int *ext, int max_groups, int *n_gr
 /* Self-test of the FP32 division of the region statements: out[i] =
  * a[i] / b[i] correctly rounded, by the statements' FMA division (which = 0),
  * by the same division on element pairs (2m, 2m + 1) as the paired FP32
- * evaluation takes it (2; n even), or by CUDA's __fdiv_rn (1); device
+ * evaluation takes it (2; n even), or by CUDA's __fdiv_rn (1); which = 3
+ * gives the reciprocal step of the statements' division alone, out[i] =
+ * 1 / b[i] correctly rounded for 2^-20 <= b[i] < 2^20 whose significand is
+ * not all ones (a is not read; other b give an undefined value).  Device
  * pointers, n >= 0; stream-ordered. */
 swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, int which, void *stream);
 

@@ -283,6 +283,30 @@ def _div_cases(seed):
     return np.concatenate(out, axis=1).astype(np.float32)
 
 
+def test_fp32_division_reciprocal_step_is_correctly_rounded_for_every_significand():
+    """The statements' division finishes with one FMA (Markstein's theorem),
+    which needs its reciprocal to be RN(1/b).  Every significand but the
+    all-ones one (which the division sends to __fdiv_rn), in the lowest,
+    middle and highest binade of the fast range: the reciprocal step equals
+    the host's RN(1/b) (1/b in float64, then rounded to float32: 1/b is never
+    within 2^-49 relative of a float32 midpoint, so the double rounding is
+    exact)."""
+    import torch
+    from paper_1107_2157_gb300 import swe
+    sig = np.arange((1 << 23) - 1, dtype=np.uint32)  # all significands but 0x7fffff
+    outs = []
+    for e in (-20, 0, 19):
+        b = ((np.uint32(127 + e) << np.uint32(23)) | sig).view(np.float32)
+        bd = torch.from_numpy(b).cuda()
+        o = torch.empty_like(bd)
+        swe.check(swe.lib().swe_selftest_div(bd.data_ptr(), bd.data_ptr(), o.data_ptr(), b.size, 3,
+                                             swe.current_stream()), "swe_selftest_div")
+        want = (1.0 / b.astype(np.float64)).astype(np.float32)
+        got = o.cpu().numpy()
+        bad = np.flatnonzero(got.view(np.uint32) != want.view(np.uint32))
+        assert bad.size == 0, (e, bad[:5], b[bad[:5]], got[bad[:5]], want[bad[:5]])
+
+
 def test_fp32_division_is_correctly_rounded():
     """The statements' FP32 division (FMA scheme with an exact rounding test),
     alone and on element pairs as the paired evaluation takes it, against
