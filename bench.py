@@ -145,8 +145,9 @@ def kernel_source_hash(kernel_name="lw_tiled_kernel<float>"):
 
 
 def traffic_per_launch(kernel_name, cells):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+    """DRAM bytes per launch (all the steps one launch advances) from the
+    committed ncu summary, if it was taken on the current kernel source;
+    else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -155,7 +156,7 @@ def traffic_per_launch(kernel_name, cells):
         return None
     if kernel_name not in KERNEL_SOURCES or d.get("source_hash") != kernel_source_hash(kernel_name):
         return None
-    return d["bytes_per_cell"] * cells
+    return d["bytes_per_cell"] * cells * d.get("steps_per_launch", 1)
 
 
 class ClockSampler:
