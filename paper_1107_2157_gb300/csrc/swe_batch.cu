@@ -91,6 +91,14 @@ __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *_
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
             const int st = STAGES > 1 ? (it & 1) : 0;
             const int tn = t + gridDim.x;
+            // the tile's record and its instance's parameters: two dependent
+            // global loads, issued before the waits so that they overlap them
+            const TileRec r = tiles[t];
+            const BatchInst *I = inst + r.inst;
+            float *o = I->buf[cur ^ 1];
+            const long long plane = I->plane, pitch = I->pitch;
+            const int nx = I->nx, ny = I->ny;
+            const Coef<float> k = I->k;
             if (STAGES > 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, st ^ 1, cur);
             if (!mbar_wait_bounded(&bars[st], (phases >> st) & 1u, err)) {
                 // give the other stage's prefetch (if any) a bounded chance to land
@@ -99,12 +107,6 @@ __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *_
             }
             phases ^= 1u << st;
 
-            const TileRec r = tiles[t];
-            const BatchInst *I = inst + r.inst;
-            float *o = I->buf[cur ^ 1];
-            const long long plane = I->plane, pitch = I->pitch;
-            const int nx = I->nx, ny = I->ny;
-            const Coef<float> k = I->k;
             const int x0 = (int)r.bx * C::TX, y0 = (int)r.by * C::TY;
             bool bad;
             if (x0 == 0 || x0 + C::TX >= nx)
@@ -159,6 +161,12 @@ __global__ void __launch_bounds__(NWARP * 32) batch_tb2_kernel(const BatchInst *
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const TileRec r = tiles[t];
             const int x0 = (int)r.bx * C::TX, y0 = (int)r.by * C::TY;
+            // the instance's parameters, loaded before the barrier and the wait
+            const BatchInst *I = inst + r.inst;
+            float *o = I->buf[cur ^ 1];
+            const long long plane = I->plane, pitch = I->pitch;
+            const int nx = I->nx, ny = I->ny;
+            const Coef<float> k = I->k;
             __syncthreads();  // the previous tile is done with the boxes
             if (threadIdx.x == 0) {
                 const CUtensorMap *m = maps + ((size_t)r.inst * 2 + cur) * 3;
@@ -170,11 +178,6 @@ __global__ void __launch_bounds__(NWARP * 32) batch_tb2_kernel(const BatchInst *
             }
             if (!__syncthreads_and(mbar_wait_bounded(bar, phase, err))) return;
             phase ^= 1u;
-            const BatchInst *I = inst + r.inst;
-            float *o = I->buf[cur ^ 1];
-            const long long plane = I->plane, pitch = I->pitch;
-            const int nx = I->nx, ny = I->ny;
-            const Coef<float> k = I->k;
             bool bad;
             if (two)
                 bad = tb2_tile_compute<float, NWARP, RY>(iH, iU, iV, mH_, mU_, mV_, o, o + plane, o + 2 * plane, nx,
