@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--passes", type=int, default=2)
     p.add_argument("--ensemble-count", type=int, default=512)
     p.add_argument("--no-tune", action="store_true", help="ensemble: default kernel variant, no autotuning")
+    p.add_argument("--ensemble-variant", type=int, default=None,
+                   help="ensemble: this kernel variant at 2 CTAs/SM (or fewer if it does not fit), no autotuning")
     p.add_argument("--skip-train", action="store_true",
                    help="learned: serve with untrained weights (kernel timing and profiling only)")
     p.add_argument("--tune-cache", default=None)
@@ -456,7 +458,9 @@ def run_ensemble(args):
         dts = b.cfl_dt(CFL, stream=sp)
         b.set_dt(dts, stream=sp)
         t0 = time.perf_counter()
-        if not args.no_tune:
+        if args.ensemble_variant is not None:
+            b.configure(args.ensemble_variant, 2)
+        elif not args.no_tune:
             b.tune(args.tune_cache, stream=sp)
         t_tune = time.perf_counter() - t0
         b.step(args.warmup, stream=sp)

@@ -49,6 +49,14 @@ struct BatchCfg {
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + 64;
 };
 
+// A warp's release of a staged tile: one arrival on the stage's "empty"
+// barrier (NWARP arrivals complete a phase), after all its lanes have read
+// the stage.
+__device__ __forceinline__ void stage_release(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 template <int NWARP, int RY, int STAGES>
 __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *__restrict__ inst,
                                                               const CUtensorMap *__restrict__ maps,
@@ -59,33 +67,49 @@ __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *_
     using B = BatchCfg<NWARP, RY, STAGES>;
     using C = typename B::C;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * B::STAGE_BYTES);
+    // per stage: "full" (the TMA boxes landed; one arrival + the bytes) and
+    // "empty" (every warp is done with the boxes; NWARP arrivals)
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * B::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NWARP);
+        }
         fence_mbar_init();
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31;
 
     auto box = [&](int stage, int f) {
         return reinterpret_cast<float *>(smem + stage * B::STAGE_BYTES + f * C::BOX_STRIDE);
     };
-    // thread 0: start the three TMA loads of tile t (buffer ``cur``) into ``stage``
-    auto issue = [&](int t, int stage, int cur) {
+    // thread 0: once every warp has released ``stage``'s previous tile, start
+    // the three TMA loads of tile t (buffer ``cur``) into it; false if that
+    // wait gave up
+    uint32_t used = 0, epar = 0;  // bit s: stage s was filled before / parity of its next release
+    auto issue = [&](int t, int stage, int cur) -> bool {
+        if ((used >> stage) & 1u) {
+            if (!mbar_wait_bounded(&empty[stage], (epar >> stage) & 1u, err)) return false;
+            epar ^= 1u << stage;
+        }
+        used |= 1u << stage;
         const TileRec r = tiles[t];
         const CUtensorMap *m = maps + ((size_t)r.inst * 2 + cur) * 3;
         const int x0 = (int)r.bx * C::TX, y0 = (int)r.by * C::TY;
-        mbar_arrive_expect_tx(&bars[stage], (uint32_t)(3 * C::BOX_BYTES));
-        tma_load_2d(box(stage, 0), m + 0, &bars[stage], x0 - C::AX, y0 - 1);
-        tma_load_2d(box(stage, 1), m + 1, &bars[stage], x0 - C::AX, y0 - 1);
-        tma_load_2d(box(stage, 2), m + 2, &bars[stage], x0 - C::AX, y0 - 1);
+        mbar_arrive_expect_tx(&full[stage], (uint32_t)(3 * C::BOX_BYTES));
+        tma_load_2d(box(stage, 0), m + 0, &full[stage], x0 - C::AX, y0 - 1);
+        tma_load_2d(box(stage, 1), m + 1, &full[stage], x0 - C::AX, y0 - 1);
+        tma_load_2d(box(stage, 2), m + 2, &full[stage], x0 - C::AX, y0 - 1);
+        return true;
     };
 
-    uint32_t phases = 0;  // bit s = parity of the next completion of stage s
+    uint32_t phases = 0;  // bit s = parity of the next completion of full[s]
     for (int step = 0; step < n_steps; ++step) {
         const int cur = (parity0 + step) & 1;
         if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) {
             fence_proxy_async_global();  // other CTAs' stores of the last step -> TMA reads
-            issue(blockIdx.x, 0, cur);
+            if (!issue(blockIdx.x, 0, cur)) return;
         }
         int it = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
@@ -99,10 +123,10 @@ __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *_
             const long long plane = I->plane, pitch = I->pitch;
             const int nx = I->nx, ny = I->ny;
             const Coef<float> k = I->k;
-            if (STAGES > 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, st ^ 1, cur);
-            if (!mbar_wait_bounded(&bars[st], (phases >> st) & 1u, err)) {
+            if (STAGES > 1 && threadIdx.x == 0 && tn < ntiles && !issue(tn, st ^ 1, cur)) return;
+            if (!mbar_wait_bounded(&full[st], (phases >> st) & 1u, err)) {
                 // give the other stage's prefetch (if any) a bounded chance to land
-                if (STAGES > 1 && tn < ntiles) mbar_wait_bounded(&bars[st ^ 1], (phases >> (st ^ 1)) & 1u, err);
+                if (STAGES > 1 && tn < ntiles) mbar_wait_bounded(&full[st ^ 1], (phases >> (st ^ 1)) & 1u, err);
                 return;
             }
             phases ^= 1u << st;
@@ -115,9 +139,12 @@ __global__ void __launch_bounds__(NWARP * 32) batch_lw_kernel(const BatchInst *_
             else
                 bad = tiled_compute<float, NWARP, RY, false>(box(st, 0), box(st, 1), box(st, 2), o, o + plane,
                                                              o + 2 * plane, nx, ny, pitch, x0, y0, k);
-            // all threads are done with this stage after the barrier
-            if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags[r.inst], SWE_FLAG_NONPOSITIVE);
-            if (STAGES == 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, 0, cur);
+            // the warp is done with this stage: flag, then release it (no
+            // CTA barrier, so a warp may run one tile ahead of the slowest)
+            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&flags[r.inst], SWE_FLAG_NONPOSITIVE);
+            __syncwarp();
+            if (lane == 0) stage_release(&empty[st]);
+            if (STAGES == 1 && threadIdx.x == 0 && tn < ntiles && !issue(tn, 0, cur)) return;
         }
         if (!grid_sync_bounded(gbar, gridDim.x, err)) return;
     }
