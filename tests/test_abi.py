@@ -59,3 +59,65 @@ def test_invalid_arguments_rejected_before_any_device_work(libswe):
     assert f(10, 10, 1.0, 1.0, float("nan"), 9.8, ctypes.byref(h)) == 1
     assert f(70000, 10, 1.0, 1.0, 0.1, 9.8, ctypes.byref(h)) == 1
     assert h.value is None
+
+
+def test_more_entry_points_reject_bad_arguments_before_device_work(libswe):
+    """Each call below fails its argument checks, which the header states run
+    before any device work, so it returns SWE_EINVAL (1) on a machine without a GPU."""
+    c_int, c_double, c_void_p, c_ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+    EINVAL = 1
+    out = c_void_p()
+    fake = c_void_p(64)  # never dereferenced: the checks reject the call first
+
+    bc = libswe.swe_batch_create
+    bc.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)] + [ctypes.POINTER(c_double)] * 3 + \
+        [c_double, ctypes.POINTER(c_void_p)]
+
+    def batch(nx, ny, dx=1.0, dy=1.0, dt=0.1, g=9.8):
+        n = len(nx)
+        ia = lambda v: (c_int * n)(*v)  # noqa: E731
+        da = lambda v: (c_double * n)(*([v] * n))  # noqa: E731
+        return bc(n, ia(nx), ia(ny), da(dx), da(dy), da(dt), g, ctypes.byref(out))
+
+    assert bc(0, None, None, None, None, None, 9.8, ctypes.byref(out)) == EINVAL
+    assert batch([64, 0], [64, 64]) == EINVAL
+    assert batch([64, 70000], [64, 64]) == EINVAL
+    assert batch([64], [64], dt=-0.1) == EINVAL
+    assert batch([64], [64], dx=float("inf")) == EINVAL
+    assert batch([64], [64], g=float("nan")) == EINVAL
+    assert out.value is None
+
+    nc = libswe.swe_net_create
+    nc.argtypes = [c_int, c_int, c_int, ctypes.POINTER(c_void_p)]
+    assert nc(0, 256, 256, ctypes.byref(out)) == EINVAL
+    assert nc(4, 8193, 256, ctypes.byref(out)) == EINVAL
+    assert nc(4, 256, 0, ctypes.byref(out)) == EINVAL
+
+    pc = libswe.swe_part_create
+    pc.argtypes = [c_int] * 4 + [c_double] * 4 + [ctypes.POINTER(c_void_p)]
+    assert pc(64, 64, 65, 1, 1.0, 1.0, 0.1, 9.8, ctypes.byref(out)) == EINVAL  # more partitions than columns
+    assert pc(4096, 4096, 64, 65, 1.0, 1.0, 0.1, 9.8, ctypes.byref(out)) == EINVAL  # > 4096 partitions
+    assert pc(64, 64, 2, 2, 1.0, 1.0, 0.0, 9.8, ctypes.byref(out)) == EINVAL
+    assert out.value is None
+
+    sd = libswe.swe_selftest_div
+    sd.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]
+    assert sd(fake, fake, fake, 16, 4, None) == EINVAL      # no such mode
+    assert sd(fake, fake, fake, 15, 2, None) == EINVAL      # pairs need an even count
+    assert sd(fake, fake, fake, -1, 0, None) == EINVAL
+    assert sd(None, fake, fake, 16, 0, None) == EINVAL
+    assert sd(fake, fake, fake, 0, 3, None) == 0            # nothing to do
+
+    sw = libswe.swe_selftest_wait
+    sw.argtypes = [c_int, c_double, c_void_p]
+    assert sw(2, 1.0, None) == EINVAL
+    assert sw(0, 0.0, None) == EINVAL
+    assert sw(1, 6000.0, None) == EINVAL
+
+    ds = libswe.swe_downsample
+    ds.argtypes = [c_int, c_void_p, c_ll, c_ll, c_ll, c_void_p, c_ll, c_ll, c_ll, c_int, c_int, c_int, c_void_p]
+    assert ds(5, fake, 0, 0, 1024, fake, 0, 0, 256, 256, 256, 1, None) == EINVAL   # factor above 4
+    assert ds(4, fake, 0, 0, 1000, fake, 0, 0, 256, 256, 256, 1, None) == EINVAL   # fine rows too short
+    rs = libswe.swe_resample
+    rs.argtypes = [c_void_p, c_ll, c_ll, c_ll, c_int, c_int, c_void_p, c_ll, c_ll, c_ll, c_int, c_int, c_int, c_void_p]
+    assert rs(fake, 0, 0, 256, 256, 256, fake, 0, 0, 512, 512, 512, 1, None) == EINVAL  # upsampling
