@@ -1,0 +1,25 @@
+"""Host-side arithmetic of bench.py's roofline fields (CPU)."""
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_traffic_is_the_dram_bytes_of_a_whole_launch():
+    """The committed ncu summary stores bytes per cell-update; the bench's
+    traffic field is per launch, i.e. times the steps one launch advances
+    (two for the temporally blocked kernel).  Entries whose counters predate
+    the current kernel sources are reported as null and skipped here."""
+    import bench
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        summary = json.load(f)
+    cells = 8192 * 8192
+    for name, e in summary.items():
+        t = bench.traffic_per_launch(name, cells)
+        if t is None:
+            assert e.get("source_hash") != bench.kernel_source_hash(name)
+            continue
+        assert abs(t - e["bytes_per_launch"]) <= 1e-9 * e["bytes_per_launch"], name
+        assert abs(e["bytes_per_cell"] * cells * e.get("steps_per_launch", 1) - e["bytes_per_launch"]) <= \
+            1e-9 * e["bytes_per_launch"], name
+    assert bench.traffic_per_launch("no such kernel", cells) is None
