@@ -6,9 +6,11 @@
 // all instances form one flat list (instance-major, so the CTAs working at
 // the same time share halo rows in L2).  CTAs stride over the list; each tile
 // is staged by TMA (three box loads on one mbarrier, double buffered so the
-// next tile's loads overlap this tile's arithmetic) and computed by the same
-// tile routine as the single-grid kernel (swe_tile.cuh).  A grid-wide barrier
-// with a bounded wait separates the time steps; all instances step together.
+// next tile's loads overlap this tile's arithmetic; each warp hands a stage
+// back on a second mbarrier once it has read it, and only the thread that
+// refills the stage waits for that) and computed by the same tile routine as
+// the single-grid kernel (swe_tile.cuh).  A grid-wide barrier with a bounded
+// wait separates the time steps; all instances step together.
 //
 // The launch is captured once per (step count, buffer parity) into a CUDA
 // graph on a private stream and replayed on the caller's stream.  Tile shape,
