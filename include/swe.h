@@ -271,7 +271,13 @@ swe_status swe_batch_state_ptr(swe_batch *b, int i, float **h, long long *plane_
  * buffer: instance i's h, hu, hv planes of ny[i] x nx[i] floats each. */
 swe_status swe_batch_copy_states(swe_batch *b, float *dst, void *stream);
 
-/* Selects a kernel variant and CTAs per SM explicitly (tests, tuning). */
+/* Selects a kernel variant (0 .. the count swe_batch_query reports for
+ * SWE_BQ_VARIANT_COUNT, minus 1) and CTAs per SM explicitly (tests, tuning,
+ * profiling); a CTA count above what fits is
+ * lowered to it.  Synchronous; call it with no step of this batch in
+ * flight, since it rewrites the tile list the kernel reads.  SWE_EINVAL for
+ * a variant out of range or ctas_per_sm < 1, SWE_EUNSUPPORTED if the
+ * variant cannot run on this device. */
 swe_status swe_batch_configure(swe_batch *b, int variant, int ctas_per_sm);
 
 typedef enum {
