@@ -1,14 +1,13 @@
 """Batched ensembles (one persistent launch over many uneven grids) against
 the FP64 oracle and against the single-grid kernel."""
 import json
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 import swe_inputs as si
-from parity import G, TOL_F32, rel_errors
+from parity import G, b32_run, f32_bar
 
 pytestmark = pytest.mark.gpu
 
@@ -46,8 +45,8 @@ def test_batch_matches_oracle_per_instance():
         for i, s in enumerate(states):
             got = b.get_state(i)
             ref = oracle.run(s.h, s.hu, s.hv, dxs[i], dys[i], dts[i], G, steps)
-            errs = rel_errors(got, ref)
-            assert max(errs) <= TOL_F32, (i, SIZES[i], errs)
+            ok, errs, errs_b32 = f32_bar(got, ref, b32_run(s, dxs[i], dys[i], dts[i], G, steps))
+            assert ok, (i, SIZES[i], errs, errs_b32)
 
 
 def test_every_variant_is_bitwise_equal_to_the_single_grid_kernel():

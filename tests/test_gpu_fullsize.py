@@ -8,7 +8,7 @@ import pytest
 import oracle
 import swe_inputs as si
 from oracle import learned, nn
-from parity import G, TOL_F32, rel_errors
+from parity import G, b32_run, f32_bar
 
 pytestmark = pytest.mark.gpu
 
@@ -38,8 +38,8 @@ def test_ensemble_512_full_size_sampled_instances():
             dt = oracle.cfl_dt(st.h, st.hu, st.hv, 1.0, 1.0, G, 0.2)
             assert dt == dts[i]
             ref = oracle.run(st.h, st.hu, st.hv, 1.0, 1.0, dt, G, steps)
-            errs = rel_errors(b.get_state(i), ref)
-            assert max(errs) <= TOL_F32, (i, sizes[i], errs)
+            ok, errs, errs_b32 = f32_bar(b.get_state(i), ref, b32_run(st, 1.0, 1.0, dt, G, steps))
+            assert ok, (i, sizes[i], errs, errs_b32)
     finally:
         b.close()
 

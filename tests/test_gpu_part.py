@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import swe_inputs as si
-from parity import G, TOL_F32, rel_errors, run_gpu
+from parity import G, b32_run, f32_bar, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,8 @@ def test_partitioned_matches_oracle():
         p.step(steps)
         got = p.get_state()
     ref = oracle.run(s.h, s.hu, s.hv, 1.0, 1.0, dt, G, steps)
-    assert max(rel_errors(got, ref)) <= TOL_F32
+    ok, errs, errs_b32 = f32_bar(got, ref, b32_run(s, 1.0, 1.0, dt, G, steps))
+    assert ok, (errs, errs_b32)
 
 
 def test_partition_arguments_are_checked():

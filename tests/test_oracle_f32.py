@@ -136,3 +136,24 @@ def test_binary32_window_run_equals_full_run_bitwise():
         i0, i1, j0, j1 = window
         for k in range(3):
             assert np.array_equal(win[k], full[k][j0 - 1:j1, i0 - 1:i1])
+
+
+@pytest.mark.parametrize("mistake", ["step1_sign", "drop_pressure", "swap_flux", "ghost_sign"])
+def test_per_step_ulp_units_separate_rounding_from_mistakes(mistake):
+    """The unit of the GPU-vs-binary32 test (tests/test_gpu_f32_ulp.py): the
+    FP64 step differs from the binary32 oracle's step by a few units, while
+    each planted mistake (in a numpy copy of the FP64 step) differs by far
+    more than the 16 units per step that test allows."""
+    from test_gpu_f32_ulp import PER_STEP, _units
+    from test_oracle_pins import _planted_step
+    s = si.smooth_flow_state(3, 40, 30).rounded_to(np.float32)
+    dx, dy = 0.8, 1.1
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, dx, dy, G, 0.3)
+    units = _units(s, dx, dy, dt)
+    b32 = oracle.run_f32(s.h, s.hu, s.hv, dx, dy, dt, G, 1)
+    good = oracle.run(s.h, s.hu, s.hv, dx, dy, dt, G, 1)
+    bad = _planted_step(mistake)(s.h, s.hu, s.hv, dx, dy, dt, G)
+    r_good = max(float(np.abs(good[k] - b32[k]).max()) / units[k] for k in range(3))
+    r_bad = max(float(np.abs(bad[k] - b32[k]).max()) / units[k] for k in range(3))
+    assert r_good <= 4.0, r_good
+    assert r_bad >= 100 * PER_STEP, (mistake, r_bad)
