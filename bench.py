@@ -31,6 +31,11 @@ G = 9.80
 N_GRID = 8192
 CFL = 0.2
 BYTES_PER_CELL_F32 = 24  # read h, hu, hv + write h, hu, hv (FP32)
+# FP32 operations of one cell-update as the kernels evaluate the step's
+# formulas (every face state and flux once): cell fluxes 7 + reciprocal,
+# x-face 17 + reciprocal, y-face 17 + reciprocal, update 12.  The three
+# reciprocals run on the special-function unit, the other 53 on the FMA pipe.
+FMA_PIPE_OPS_PER_CELL_UPDATE = 53
 METRIC = "SWE cell-updates/s, % HBM roofline; learned-coarse vs plain at equal error"
 UNIT = "cell-updates/s"
 
@@ -46,6 +51,8 @@ def parse():
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
     p.add_argument("--variant", type=int, default=None, help="two-step kernel tile shape 0..3 (with --kernel 3)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="grid: leave out the ensemble and FP64 sub-records of the default line")
     p.add_argument("--px", type=int, default=2, help="partitioned: partitions along x")
     p.add_argument("--py", type=int, default=2, help="partitioned: partitions along y")
     p.add_argument("--region-variant", type=int, default=0, help="region: tile shape (0 = default)")
@@ -219,14 +226,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(target_s=10.0, max_cells=2048 * 2048):
-    """Time the FP64 oracle on all host cores on a window of the 8192x8192
-    initial state.  Returns (cell-updates/s, threads, description)."""
+def cpu_oracle_rate(target_s=10.0, max_cells=2048 * 2048, threads=None):
+    """Time the FP64 oracle on ``threads`` host cores (default: all) on a
+    window of the 8192x8192 initial state.  Returns (cell-updates/s,
+    threads, description)."""
     import numpy as np
     import oracle
     import swe_inputs as si
 
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     m = int(math.sqrt(max_cells))
     c0 = N_GRID // 2 - m // 2
@@ -242,8 +250,10 @@ def cpu_oracle_rate(target_s=10.0, max_cells=2048 * 2048):
     oracle.run_padded(H, U, V, 1.0, 1.0, dt, G, steps)
     el = time.perf_counter() - t0
     rate = m * m * steps / el
-    desc = ("FP64 C oracle (OpenMP over rows), %dx%d central window of the 8192x8192 initial state "
-            "with reflective walls, %d steps in %.1f s" % (m, m, steps, el))
+    desc = ("FP64 C oracle (%s), %dx%d central window of the 8192x8192 initial state "
+            "with reflective walls, %d steps in %.1f s"
+            % ("OpenMP over rows, %d threads" % threads if threads > 1 else "one thread", m, m, steps, el))
+    oracle.set_threads(1)
     return rate, threads, desc
 
 
@@ -396,16 +406,26 @@ def run_ours(args):
     value = whole_job_rate(ws, cells, args.steps, t_job)
     per_launch = t_steps / max(1, launches)
     peak, peak_kind = measured_peaks()
-    # algorithmic bytes of one launch: bytes per cell-update of the layout x
-    # cells x steps the launch advances (an odd last step of the two-step
-    # kernel is a one-step launch, counted as two here: a slight overstatement)
-    alg_bytes = bytes_per_update * cells * steps_per_launch
+    # algorithmic bytes of one launch: the launch reads the state once and
+    # writes it once, whatever number of steps it takes in between (the
+    # two-step kernel: 24 B per cell = 12 B per cell-update); the one-step
+    # equivalent (24 B per cell-update) is reported as effective_gbs
+    alg_bytes = bytes_per_update * cells
     achieved = alg_bytes / per_launch / 1e9
+    effective = bytes_per_update * cells * steps_per_launch / per_launch / 1e9
     tr = traffic_per_launch(kname, cells)
+    fp32_fma_rate = max(swe.swe_probe_rate(swe.SWE_PROBE_FP32), swe.swe_probe_rate(swe.SWE_PROBE_FP32X2))
+    alu_ops = FMA_PIPE_OPS_PER_CELL_UPDATE * cells * steps_per_launch / per_launch
+    extra = {}
+    if ws == 1 and not args.no_extra:
+        extra["ensemble_512"] = ensemble_record(args)
+        extra["fp64_8192"] = fp64_record(args, peak)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         rate, thr, desc = cpu_oracle_rate()
-        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+        rate1, _, desc1 = cpu_oracle_rate(target_s=5.0, max_cells=1024 * 1024, threads=1)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+               "single_core": {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc1}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps, "higher_is_better": True,
@@ -416,8 +436,17 @@ def run_ours(args):
                      "kernel": "%s (%d step%s per launch)" % (kname, steps_per_launch,
                                                              "s" if steps_per_launch > 1 else ""),
                      "algorithmic_bytes_per_launch": alg_bytes,
-                     "algorithmic_bytes_per_cell_update": bytes_per_update,
-                     "launch_ms": per_launch * 1e3, "peak_source": peak_kind + " hbm_gbs (copy)"},
+                     "algorithmic_bytes_per_cell_update": bytes_per_update / steps_per_launch,
+                     "effective_gbs": effective,
+                     "effective_note": "%d B per cell-update (the one-step compulsory traffic) x cell-updates per "
+                                       "launch / launch time; above the HBM peak when a launch takes several steps"
+                                       % bytes_per_update,
+                     "launch_ms": per_launch * 1e3, "peak_source": peak_kind + " hbm_gbs (copy)",
+                     "alu": {"achieved": alu_ops / 1e9, "peak": fp32_fma_rate / 1e9, "unit": "G FMA-pipe ops/s",
+                             "frac": alu_ops / fp32_fma_rate,
+                             "ops_per_cell_update": FMA_PIPE_OPS_PER_CELL_UPDATE,
+                             "peak_source": "measured FP32 FMA rate (swe_probe_rate, the larger of scalar and "
+                                            "packed f32x2), lane operations per second"}},
         "e2e": {"value": whole_job_rate(ws, cells, args.steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * 4 * cells / args.steps, "d2h_bytes_per_step": 3 * 4 * cells / args.steps,
                 "note": "the job through the C ABI from pinned host buffers: host->device state (3 x FP32 "
@@ -428,7 +457,101 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "checks": {"status": swe.strerror(status), "mass": mass, "mass_e2e": mass2, "dt": dt},
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def ensemble_record(args, steps=500):
+    """The 512-grid ensemble (nx, ny uniform in [64, 1024], seed 2), tuned
+    persistent launch, ``steps`` steps timed with CUDA events: a compact
+    record for the default bench line."""
+    import numpy as np
+    import torch
+
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import Batch, swe
+
+    sizes = si.ensemble_sizes(seed=2, count=512)
+    states = [si.ensemble_state(2, i, nx, ny) for i, (nx, ny) in enumerate(sizes)]
+    cells = sum(nx * ny for nx, ny in sizes)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    with Batch(sizes, 1.0, 1.0, 0.01, G) as b:
+        def load():
+            for i, st in enumerate(states):
+                b.set_state(i, *(a.astype(np.float32) for a in (st.h, st.hu, st.hv)), stream=sp)
+        load()
+        b.set_dt(b.cfl_dt(CFL, stream=sp), stream=sp)
+        t0 = time.perf_counter()
+        b.tune(args.tune_cache, stream=sp)
+        t_tune = time.perf_counter() - t0
+        b.step(4, stream=sp)
+        load()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps, stream=sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        rc, flags = b.status(stream=sp)
+        depth = int(b.query(swe.SWE_BQ_DEPTH))
+        tuned = {k: int(b.query(getattr(swe, "SWE_BQ_" + k))) for k in ("VARIANT", "CTAS_PER_SM", "TILE_X",
+                                                                          "TILE_Y", "STAGES", "DEPTH")}
+    peak, kind = measured_peaks()
+    rate = cells * steps / t
+    bpu = BYTES_PER_CELL_F32 / depth
+    return {"workload": "512 instances, nx, ny uniform in [64, 1024] (seed 2), 4 bumps each, per-instance FP64 "
+                        "CFL 0.2 dt, FP32, %d steps in one persistent graph-captured launch" % steps,
+            "value": rate, "unit": UNIT, "ms_per_step": 1e3 * t / steps, "cells": cells,
+            "roofline": {"bound": "hbm", "achieved": bpu * rate / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bpu * rate / 1e9 / peak, "algorithmic_bytes_per_cell_update": bpu,
+                         "peak_source": kind + " hbm_gbs (copy)"},
+            "tuned": tuned, "tune_s": t_tune, "status": int(rc), "flags_set": int((flags != 0).sum())}
+
+
+def fp64_record(args, peak, steps=20):
+    """The 8192x8192 grid of the default workload in FP64 (one-step kernel),
+    ``steps`` steps timed with CUDA events, against the HBM peak and the
+    measured FP64 FMA rate."""
+    import numpy as np
+    import torch
+
+    import swe_inputs as si
+    from paper_1107_2157_gb300 import Grid, swe
+
+    n = args.n
+    cells = n * n
+    h = torch.from_numpy(si.large_grid_state(seed=1, n=n).h).cuda()
+    z = torch.zeros_like(h)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    with Grid(n, n, 1.0, 1.0, 0.01, G, dtype="f64") as grid:
+        grid.set_state(h, z, z, stream=sp)
+        grid.set_dt(grid.cfl_dt(CFL, stream=sp))
+        grid.step(2, stream=sp)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grid.step(steps, stream=sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        status = grid.check(stream=sp)
+    del h, z
+    fp64_rate = swe.swe_probe_rate(swe.SWE_PROBE_FP64)
+    rate = cells * steps / t
+    ops = FMA_PIPE_OPS_PER_CELL_UPDATE + 3  # the three reciprocals are FP64 divisions here
+    return {"workload": "%dx%d FP64, the default workload's initial state, %d steps" % (n, n, steps),
+            "value": rate, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
+            "hbm": {"achieved": 48 * rate / 1e9, "peak": peak, "unit": "GB/s", "frac": 48 * rate / 1e9 / peak,
+                    "algorithmic_bytes_per_cell_update": 48},
+            "alu": {"achieved": ops * rate / 1e9, "peak": fp64_rate / 1e9, "unit": "G FP64 ops/s",
+                    "frac": ops * rate / fp64_rate, "ops_per_cell_update": ops,
+                    "note": "the formulas' FP64 operations, a division counted as one; the hardware spends "
+                            "several FMA-pipe operations on each IEEE division, so this fraction is a lower bound "
+                            "of the pipe's use", "peak_source": "measured FP64 FMA rate (swe_probe_rate)"},
+            "status": swe.strerror(status)}
 
 
 # ---------------------------------------------------------------------------

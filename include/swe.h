@@ -263,6 +263,19 @@ swe_status swe_batch_tune(swe_batch *b, const char *cache_path, void *stream);
  */
 swe_status swe_selftest_wait(int which, double limit_ms, void *stream);
 
+/*
+ * swe_probe_rate (no counterpart in the paper): measures the current
+ * device's arithmetic throughput, the peak against which the ALU-bound
+ * kernels' fractions are stated.  kind 0: scalar FP32 FMA, 1: packed f32x2
+ * FMA (two lanes per instruction), 2: FP64 FMA.  Runs independent FMA
+ * chains in 8 CTAs of 256 threads per SM for a few milliseconds on a
+ * private stream, times the last of three launches with CUDA events and
+ * writes FMAs per second (lane operations; an FMA is two flops) to
+ * *rate_out.  Synchronous; changes no device setting.  SWE_EINVAL for an
+ * unknown kind or a null pointer, SWE_ECUDA on a CUDA error.
+ */
+swe_status swe_probe_rate(int kind, double *rate_out);
+
 /* Device address of instance i's h plane in the current buffer, and the
  * plane stride and row pitch in floats (hu, hv follow at +1, +2 planes). */
 swe_status swe_batch_state_ptr(swe_batch *b, int i, float **h, long long *plane_stride, long long *pitch);

@@ -5,10 +5,17 @@
 // of blocks per grid writes one FP64 partial per block to a scratch buffer,
 // then one block per grid combines that grid's partials in a fixed order.
 // The assignment of cells to threads and the combining tree depend only on
-// the grid's size and the block count, so results are bitwise reproducible.  The CFL per-cell terms use explicitly rounded FP64
-// operations (no contraction), so the minimum is the exact minimum of
-// correctly rounded per-cell bounds.
+// the grid's size and the block count, so results are bitwise reproducible.
+// The CFL per-cell terms use explicitly rounded FP64 operations (no
+// contraction), so the minimum is the exact minimum of correctly rounded
+// per-cell bounds.
+//
+// GB300 runs FP64 arithmetic at a small fraction of its FP32 and integer
+// rates, so the FP32 reductions keep FP64 operations off the per-cell path:
+// the mass sums FP32 depths exactly in 64-bit integers (ExactSum32) and the
+// CFL step screens cells with FP32 estimates before any FP64 evaluation.
 #include "swe_device.cuh"
+#include "swe_exact_sum.h"
 
 namespace swe {
 
@@ -68,40 +75,57 @@ __device__ __forceinline__ RedGrid red_grid(const RedGrid &one, const RedGrid *_
 
 // Mass partials.  Each block takes rows blockIdx.x, blockIdx.x + gridDim.x,
 // ...; with VEC the threads read 16-byte vectors (4 FP32 / 2 FP64 values,
-// the row base and stride being 16-byte aligned) and the row tail scalar.
-// Two FP64 accumulators per thread keep the adds independent.
+// the row base and stride being 16-byte aligned), four per thread in flight,
+// and the row tail scalar.  FP32 depths are summed exactly (ExactSum32);
+// FP64 depths in two FP64 accumulators per thread.
 template <typename T, bool VEC, bool MANY>
 __global__ void __launch_bounds__(kRedThreads) mass_partial_kernel(RedGrid one, const RedGrid *__restrict__ many,
                                                                    double *partial)
 {
     constexpr int N = 16 / sizeof(T);
+    constexpr bool F32 = sizeof(T) == 4;
     const RedGrid G = red_grid<MANY>(one, many);
     const T *H = static_cast<const T *>(G.h);
     double s0 = 0.0, s1 = 0.0;
+    ExactSum32 ex;
     for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
         const T *row = H + (size_t)j * (size_t)G.pitch;
         int i0 = 0;
         if (VEC) {
             const int nv = G.nx / N;
-#pragma unroll 4
-            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-                if constexpr (sizeof(T) == 4) {
-                    const float4 x = __ldg(reinterpret_cast<const float4 *>(row) + v);
-                    s0 += (double)x.x;
-                    s1 += (double)x.y;
-                    s0 += (double)x.z;
-                    s1 += (double)x.w;
+            for (int v0 = threadIdx.x; v0 < nv; v0 += 4 * blockDim.x) {
+                if constexpr (F32) {
+                    float4 x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int v = v0 + q * blockDim.x;
+                        x[q] = v < nv ? __ldg(reinterpret_cast<const float4 *>(row) + v) : make_float4(0, 0, 0, 0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (v0 + q * (int)blockDim.x < nv) ex.add4(x[q].x, x[q].y, x[q].z, x[q].w);
                 } else {
-                    const double2 x = __ldg(reinterpret_cast<const double2 *>(row) + v);
-                    s0 += (double)x.x;
-                    s1 += (double)x.y;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int v = v0 + q * blockDim.x;
+                        if (v < nv) {
+                            const double2 x = __ldg(reinterpret_cast<const double2 *>(row) + v);
+                            s0 += (double)x.x;
+                            s1 += (double)x.y;
+                        }
+                    }
                 }
             }
             i0 = nv * N;
         }
-        for (int i = i0 + threadIdx.x; i < G.nx; i += blockDim.x) s0 += (double)row[i];
+        for (int i = i0 + threadIdx.x; i < G.nx; i += blockDim.x) {
+            if constexpr (F32)
+                ex.add1((float)row[i]);
+            else
+                s0 += (double)row[i];
+        }
     }
-    const double s = block_reduce<false>(s0 + s1);
+    const double s = block_reduce<false>(F32 ? ex.value() : s0 + s1);
     if (threadIdx.x == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
@@ -143,30 +167,77 @@ __device__ __forceinline__ bool cell_bad(T h, T u, T v)
     return !(h > T(0)) || !isfinite(h) || !isfinite(u) || !isfinite(v);
 }
 
-template <typename T, bool MANY>
+// FP32 estimate of a cell's sx and sy (pass 1 and the pass-2 screen use
+// this one function: explicitly rounded operations, the same bits in both).
+__device__ __forceinline__ void cfl_estimate(float h, float u, float v, float g32, float &ex, float &ey)
+{
+    const float inv = rcp(h);
+    const float c = __fsqrt_rn(__fmul_rn(g32, h));
+    ex = __fadd_rn(c, fabsf(__fmul_rn(u, inv)));
+    ey = __fadd_rn(c, fabsf(__fmul_rn(v, inv)));
+}
+
+// Visits every cell of the block's rows (rows blockIdx.x, blockIdx.x +
+// gridDim.x, ...) in the data's own type.  With VEC (FP32 planes, 16-byte
+// aligned rows) a thread loads two 16-byte vectors of each plane at a time
+// and takes the row tail one cell at a time.
+template <typename T, bool VEC, typename F>
+__device__ __forceinline__ void for_cells(const RedGrid &G, F &&f)
+{
+    const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
+    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+        const size_t ro = (size_t)j * (size_t)G.pitch;
+        int i0 = 0;
+        if constexpr (VEC && sizeof(T) == 4) {
+            const float4 *h4 = reinterpret_cast<const float4 *>(H + ro);
+            const float4 *u4 = reinterpret_cast<const float4 *>(U + ro);
+            const float4 *v4 = reinterpret_cast<const float4 *>(V + ro);
+            const int nv = G.nx / 4;
+            for (int v0 = threadIdx.x; v0 < nv; v0 += 2 * blockDim.x) {
+                float4 a[2], b[2], c[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int k = v0 + q * blockDim.x;
+                    if (k < nv) {
+                        a[q] = __ldg(h4 + k);
+                        b[q] = __ldg(u4 + k);
+                        c[q] = __ldg(v4 + k);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (v0 + q * (int)blockDim.x < nv) {
+                        f(a[q].x, b[q].x, c[q].x);
+                        f(a[q].y, b[q].y, c[q].y);
+                        f(a[q].z, b[q].z, c[q].z);
+                        f(a[q].w, b[q].w, c[q].w);
+                    }
+                }
+            }
+            i0 = nv * 4;
+        }
+        for (int i = i0 + threadIdx.x; i < G.nx; i += blockDim.x) f(H[ro + i], U[ro + i], V[ro + i]);
+    }
+}
+
+template <typename T, bool VEC, bool MANY>
 __global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(RedGrid one, const RedGrid *__restrict__ many,
                                                                 float g32, double *scratch)
 {
     const RedGrid G = red_grid<MANY>(one, many);
-    const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
     const size_t P = (size_t)gridDim.x * gridDim.y;
     float ax = 0.0f, ay = 0.0f;
     double bad = 0.0;
-    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
-        const size_t ro = (size_t)j * (size_t)G.pitch;
-        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
-            const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
-            if (cell_bad<T>(h, u, v)) {
-                bad += 1.0;
-                continue;
-            }
-            const float hf = (float)h;
-            const float inv = rcp(hf);
-            const float c = sqrtf(g32 * hf);
-            ax = fmaxf(ax, c + fabsf((float)u * inv));
-            ay = fmaxf(ay, c + fabsf((float)v * inv));
+    for_cells<T, VEC>(G, [&](T h, T u, T v) {
+        if (cell_bad<T>(h, u, v)) {
+            bad += 1.0;
+            return;
         }
-    }
+        float ex, ey;
+        cfl_estimate((float)h, (float)u, (float)v, g32, ex, ey);
+        ax = fmaxf(ax, ex);
+        ay = fmaxf(ay, ey);
+    });
     ax = (float)block_reduce<false, true>((double)ax);
     ay = (float)block_reduce<false, true>((double)ay);
     bad = block_reduce<false, false>(bad);
@@ -207,31 +278,28 @@ __device__ __forceinline__ double exact_speed(double g, double h, double m)
     return __dadd_rn(__dsqrt_rn(__dmul_rn(g, h)), fabs(__ddiv_rn(m, h)));
 }
 
-template <typename T, bool MANY>
+// Pass 2.  A block whose pass-1 maxima (same rows, same estimates) lie
+// below both thresholds holds no candidate and reads nothing.
+template <typename T, bool VEC, bool MANY>
 __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, const RedGrid *__restrict__ many,
                                                                 float g32, double g, double *scratch)
 {
     const RedGrid G = red_grid<MANY>(one, many);
-    const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
     const size_t n = gridDim.y;
     const size_t P = (size_t)gridDim.x * n;
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     const double *th = scratch + 3 * P + 3 * (size_t)blockIdx.y;
     // thresholds as floats rounded toward -inf: the screen keeps every
     // candidate the FP64 threshold keeps, and compares in FP32
     const float thx = __double2float_rd(th[0]), thy = __double2float_rd(th[1]);
     double sx = 0.0, sy = 0.0;
-    T lhx = T(-1), lux = T(0), lhy = T(-1), lvy = T(0);  // last exactly evaluated inputs
-    double lsx = 0.0, lsy = 0.0;
-    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
-        const size_t ro = (size_t)j * (size_t)G.pitch;
-        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
-            const T h = H[ro + i], u = U[ro + i], v = V[ro + i];
-            if (cell_bad<T>(h, u, v)) continue;
-            const float hf = (float)h;
-            const float inv = rcp(hf);
-            const float c = sqrtf(g32 * hf);
-            const float ex = c + fabsf((float)u * inv);
-            const float ey = c + fabsf((float)v * inv);
+    if (!((float)scratch[b] < thx && (float)scratch[P + b] < thy)) {
+        T lhx = T(-1), lux = T(0), lhy = T(-1), lvy = T(0);  // last exactly evaluated inputs
+        double lsx = 0.0, lsy = 0.0;
+        for_cells<T, VEC>(G, [&](T h, T u, T v) {
+            if (cell_bad<T>(h, u, v)) return;
+            float ex, ey;
+            cfl_estimate((float)h, (float)u, (float)v, g32, ex, ey);
             if (ex >= thx) {
                 if (!(h == lhx && u == lux)) {
                     lhx = h;
@@ -248,12 +316,11 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, con
                 }
                 sy = fmax(sy, lsy);
             }
-        }
+        });
+        sx = block_reduce<false, true>(sx);
+        sy = block_reduce<false, true>(sy);
     }
-    sx = block_reduce<false, true>(sx);
-    sy = block_reduce<false, true>(sy);
     if (threadIdx.x == 0) {
-        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
         scratch[3 * P + 3 * n + b] = sx;
         scratch[4 * P + 3 * n + b] = sy;
     }
@@ -323,15 +390,15 @@ cudaError_t launch_mass_many(const RedGrid *grids_dev, int n, int B, double *scr
     return cudaGetLastError();
 }
 
-template <typename T, bool MANY>
+template <typename T, bool VEC, bool MANY>
 static void cfl_launch(const RedGrid &one, const RedGrid *many, int n, int B, double g, double cfl, double *scratch,
                        double *out, cudaStream_t s)
 {
     const dim3 grid(B, n);
     const float g32 = (float)g;
-    cfl_pass1_kernel<T, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, scratch);
+    cfl_pass1_kernel<T, VEC, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, scratch);
     cfl_pass1_final_kernel<<<n, 1024, 0, s>>>(scratch, n, B);
-    cfl_pass2_kernel<T, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, g, scratch);
+    cfl_pass2_kernel<T, VEC, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, g, scratch);
     cfl_final_kernel<MANY><<<n, 1024, 0, s>>>(one, many, scratch, n, B, cfl, out);
 }
 
@@ -341,17 +408,20 @@ cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, i
     RedGrid one{H, U, V, pitch, nx, ny, dx, dy};
     const int B = red_blocks(ny);
     if (dtype == SWE_F64)
-        cfl_launch<double, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+        cfl_launch<double, false, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+    else if (plane_vec_ok(H, pitch, 4) && plane_vec_ok(U, pitch, 4) && plane_vec_ok(V, pitch, 4))
+        cfl_launch<float, true, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
     else
-        cfl_launch<float, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+        cfl_launch<float, false, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cfl_many(const RedGrid *grids_dev, int n, int B, double g, double cfl, double *scratch,
                             double *out_dev, cudaStream_t s)
 {
+    // batched planes are FP32 with 128-byte aligned rows
     RedGrid none{};
-    cfl_launch<float, true>(none, grids_dev, n, B, g, cfl, scratch, out_dev, s);
+    cfl_launch<float, true, true>(none, grids_dev, n, B, g, cfl, scratch, out_dev, s);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ _SIGS = {
     "swe_batch_configure": (_i, [_vp, _i, _i]),
     "swe_batch_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_selftest_wait": (_i, [_i, _d, _vp]),
+    "swe_probe_rate": (_i, [_i, ctypes.POINTER(_d)]),
     "swe_batch_state_ptr": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
     "swe_batch_copy_states": (_i, [_vp, _vp, _vp]),
     "swe_net_param_count": (ctypes.c_size_t, []),
@@ -221,6 +222,16 @@ def swe_mass_noalloc(dtype, h, nx, ny, ld, dx, dy, mass_dev, stream=None) -> Non
 
 
 # --- marshalling helpers -----------------------------------------------------------------
+
+SWE_PROBE_FP32, SWE_PROBE_FP32X2, SWE_PROBE_FP64 = 0, 1, 2
+
+
+def swe_probe_rate(kind) -> float:
+    """Measured FMAs per second of the current device (kind: SWE_PROBE_*)."""
+    r = ctypes.c_double(0.0)
+    check(lib().swe_probe_rate(int(kind), ctypes.byref(r)), "swe_probe_rate")
+    return r.value
+
 
 def current_stream():
     """cudaStream_t of torch's current stream (as an int), or None."""
