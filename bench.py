@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
-    p.add_argument("--variant", type=int, default=None, help="two-step kernel tile shape 0..3 (with --kernel 3)")
+    p.add_argument("--variant", type=int, default=None, help="two-step kernel shape 0..4 (with --kernel 3; 4 = persistent 8x4)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="grid: leave out the ensemble and FP64 sub-records of the default line")

@@ -203,7 +203,7 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     // gain nothing at GB300's FP64 rate).
     c->kernel = o.kernel != SWE_KERNEL_AUTO ? o.kernel : (o.dtype == SWE_F32 ? SWE_KERNEL_TEMPORAL : SWE_KERNEL_TILED);
     c->depth = c->kernel == SWE_KERNEL_TEMPORAL ? 2 : 1;
-    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 4) ? o.reserved[0] - 1 : 1;
+    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 5) ? o.reserved[0] - 1 : 4;
 
     const size_t bytes = 3 * c->plane * c->esize;
     swe_status st = SWE_OK;

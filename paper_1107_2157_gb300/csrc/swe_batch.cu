@@ -372,12 +372,7 @@ static swe_status st_of(cudaError_t e)
 
 static Coef<float> coef_of(double dx, double dy, double dt, double g)
 {
-    Coef<float> k;
-    k.hx = (float)(0.5 * dt / dx);
-    k.hy = (float)(0.5 * dt / dy);
-    k.lx = (float)(dt / dx);
-    k.ly = (float)(dt / dy);
-    k.hg = (float)(0.5 * g);
+    const Coef<float> k = make_coef<float>(dx, dy, dt, g);
     return k;
 }
 

@@ -184,12 +184,35 @@ __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// Coefficients of the step.  The face functions below carry every face
+// quantity doubled: with s = a + b and d a flux difference, the half step's
+// 0.5 s + (0.5 dt/dx) d is evaluated as s + (dt/dx) d, which is exactly twice
+// it in every rounding (a factor of two is exact, and lx = 2 hx exactly), and
+// the update then takes (0.5 dt/dx) times the difference of doubled fluxes,
+// which is exactly dt/dx times the difference of the fluxes.  This saves the
+// three halvings of each face and gives the same bits as the plain form,
+// provided the reciprocal of 2x is half the reciprocal of x: true of IEEE
+// division and of rcp.approx (the latter checked on the GPU by the tests).
 template <typename T>
 struct Coef {
-    T hx, hy;  // 0.5 dt/dx, 0.5 dt/dy: half-step factors (step 1)
-    T lx, ly;  // dt/dx, dt/dy: full-step factors (step 2)
-    T hg;      // g/2: the hydrostatic pressure g h^2 / 2
+    T hx, hy;  // 0.5 dt/dx, 0.5 dt/dy: the update's factors on doubled fluxes
+    T lx, ly;  // dt/dx, dt/dy: the doubled face states' factors
+    T hg;      // g/2: the hydrostatic pressure g h^2 / 2 of a cell
+    T qg;      // g/4 (= hg/2 exactly): the pressure of a doubled face state
 };
+
+template <typename T>
+__host__ __device__ inline Coef<T> make_coef(double dx, double dy, double dt, double g)
+{
+    Coef<T> k;
+    k.hx = (T)(0.5 * dt / dx);
+    k.hy = (T)(0.5 * dt / dy);
+    k.lx = (T)(dt / dx);
+    k.ly = (T)(dt / dy);
+    k.hg = (T)(0.5 * g);
+    k.qg = k.hg * (T)0.5;
+    return k;
+}
 
 // A cell with its physical fluxes (Sec. 3 conservation laws):
 //   F = (U, U^2/H + g H^2/2, U V/H),  G = (V, U V/H, V^2/H + g H^2/2).
@@ -243,49 +266,50 @@ struct Flux3 {
 };
 
 // Step 1 on an x-face between cells L (left) and R (right), then the
-// x-flux F evaluated at the face state (step 2's input).
+// x-flux F evaluated at the face state (step 2's input), both doubled (see
+// Coef): the face state is 2 (0.5 (L + R) + (0.5 dt/dx) (F(L) - F(R))) and
+// the result is 2 F of it.
 template <typename T>
 __device__ __forceinline__ Flux3<T> xface_flux(const CellQ<T> &L, const CellQ<T> &R, const Coef<T> &k)
 {
-    const T half = T(0.5);
-    const T Hf = fma(k.hx, L.u - R.u, mul_rn(half, L.h + R.h));
-    const T Uf = fma(k.hx, L.f2 - R.f2, mul_rn(half, L.u + R.u));
-    const T Vf = fma(k.hx, L.f3 - R.f3, mul_rn(half, L.v + R.v));
+    const T Hf = fma(k.lx, L.u - R.u, L.h + R.h);
+    const T Uf = fma(k.lx, L.f2 - R.f2, L.u + R.u);
+    const T Vf = fma(k.lx, L.f3 - R.f3, L.v + R.v);
     const T inv = rcp(Hf);
     const T uf = mul_rn(Uf, inv);
     Flux3<T> F;
     F.a = Uf;
-    F.b = fma(Uf, uf, mul_rn(mul_rn(k.hg, Hf), Hf));
+    F.b = fma(Uf, uf, mul_rn(mul_rn(k.qg, Hf), Hf));
     F.c = mul_rn(Vf, uf);
     return F;
 }
 
 // Step 1 on a y-face between cells D (below) and U (above), then the
-// y-flux G at the face state.
+// y-flux G at the face state, both doubled as in xface_flux.
 template <typename T>
 __device__ __forceinline__ Flux3<T> yface_flux(const CellQ<T> &D, const CellQ<T> &U, const Coef<T> &k)
 {
-    const T half = T(0.5);
-    const T Hf = fma(k.hy, D.v - U.v, mul_rn(half, D.h + U.h));
-    const T Uf = fma(k.hy, D.f3 - U.f3, mul_rn(half, D.u + U.u));
-    const T Vf = fma(k.hy, D.g3 - U.g3, mul_rn(half, D.v + U.v));
+    const T Hf = fma(k.ly, D.v - U.v, D.h + U.h);
+    const T Uf = fma(k.ly, D.f3 - U.f3, D.u + U.u);
+    const T Vf = fma(k.ly, D.g3 - U.g3, D.v + U.v);
     const T inv = rcp(Hf);
     const T vf = mul_rn(Vf, inv);
     Flux3<T> G;
     G.a = Vf;
     G.b = mul_rn(Uf, vf);
-    G.c = fma(Vf, vf, mul_rn(mul_rn(k.hg, Hf), Hf));
+    G.c = fma(Vf, vf, mul_rn(mul_rn(k.qg, Hf), Hf));
     return G;
 }
 
-// Step 2: conservative update of one cell from its four face fluxes.
+// Step 2: conservative update of one cell from its four (doubled) face
+// fluxes: u - (dt/dx)(F_r - F_l) - (dt/dy)(G_u - G_d).
 template <typename T>
 __device__ __forceinline__ void lw_update(T &h, T &u, T &v, const Flux3<T> &Fl, const Flux3<T> &Fr,
                                           const Flux3<T> &Gd, const Flux3<T> &Gu, const Coef<T> &k)
 {
-    h = fma(k.ly, Gd.a - Gu.a, fma(k.lx, Fl.a - Fr.a, h));
-    u = fma(k.ly, Gd.b - Gu.b, fma(k.lx, Fl.b - Fr.b, u));
-    v = fma(k.ly, Gd.c - Gu.c, fma(k.lx, Fl.c - Fr.c, v));
+    h = fma(k.hy, Gd.a - Gu.a, fma(k.hx, Fl.a - Fr.a, h));
+    u = fma(k.hy, Gd.b - Gu.b, fma(k.hx, Fl.b - Fr.b, u));
+    v = fma(k.hy, Gd.c - Gu.c, fma(k.hx, Fl.c - Fr.c, v));
 }
 
 // ---------------------------------------------------------------------------
@@ -381,12 +405,12 @@ struct Flux2 {
 };
 // the coefficients broadcast to both lanes
 struct Coef2 {
-    F2 hx, hy, lx, ly, hg, half;
+    F2 hx, hy, lx, ly, hg, qg;
 };
 __device__ __forceinline__ Coef2 coef2(const Coef<float> &k)
 {
     return {pack2(k.hx, k.hx), pack2(k.hy, k.hy), pack2(k.lx, k.lx), pack2(k.ly, k.ly), pack2(k.hg, k.hg),
-            pack2(0.5f, 0.5f)};
+            pack2(k.qg, k.qg)};
 }
 
 // make_cell on two cells
@@ -432,14 +456,14 @@ __device__ __forceinline__ CellQ<float> cell_hi(const CellQ2 &c)
 // xface_flux on two faces
 __device__ __forceinline__ Flux2 xface_flux2(const CellQ2 &L, const CellQ2 &R, const Coef2 &k)
 {
-    const F2 Hf = fma2(k.hx, sub2(L.u, R.u), mul2(k.half, add2(L.h, R.h)));
-    const F2 Uf = fma2(k.hx, sub2(L.f2, R.f2), mul2(k.half, add2(L.u, R.u)));
-    const F2 Vf = fma2(k.hx, sub2(L.f3, R.f3), mul2(k.half, add2(L.v, R.v)));
+    const F2 Hf = fma2(k.lx, sub2(L.u, R.u), add2(L.h, R.h));
+    const F2 Uf = fma2(k.lx, sub2(L.f2, R.f2), add2(L.u, R.u));
+    const F2 Vf = fma2(k.lx, sub2(L.f3, R.f3), add2(L.v, R.v));
     const F2 inv = rcp2(Hf);
     const F2 uf = mul2(Uf, inv);
     Flux2 F;
     F.a = Uf;
-    F.b = fma2(Uf, uf, mul2(mul2(k.hg, Hf), Hf));
+    F.b = fma2(Uf, uf, mul2(mul2(k.qg, Hf), Hf));
     F.c = mul2_rn(Vf, uf);  // differenced by the update
     return F;
 }
@@ -447,15 +471,15 @@ __device__ __forceinline__ Flux2 xface_flux2(const CellQ2 &L, const CellQ2 &R, c
 // yface_flux on two faces
 __device__ __forceinline__ Flux2 yface_flux2(const CellQ2 &D, const CellQ2 &U, const Coef2 &k)
 {
-    const F2 Hf = fma2(k.hy, sub2(D.v, U.v), mul2(k.half, add2(D.h, U.h)));
-    const F2 Uf = fma2(k.hy, sub2(D.f3, U.f3), mul2(k.half, add2(D.u, U.u)));
-    const F2 Vf = fma2(k.hy, sub2(D.g3, U.g3), mul2(k.half, add2(D.v, U.v)));
+    const F2 Hf = fma2(k.ly, sub2(D.v, U.v), add2(D.h, U.h));
+    const F2 Uf = fma2(k.ly, sub2(D.f3, U.f3), add2(D.u, U.u));
+    const F2 Vf = fma2(k.ly, sub2(D.g3, U.g3), add2(D.v, U.v));
     const F2 inv = rcp2(Hf);
     const F2 vf = mul2(Vf, inv);
     Flux2 G;
     G.a = Vf;
     G.b = mul2_rn(Uf, vf);  // differenced by the update
-    G.c = fma2(Vf, vf, mul2(mul2(k.hg, Hf), Hf));
+    G.c = fma2(Vf, vf, mul2(mul2(k.qg, Hf), Hf));
     return G;
 }
 
@@ -463,9 +487,9 @@ __device__ __forceinline__ Flux2 yface_flux2(const CellQ2 &D, const CellQ2 &U, c
 __device__ __forceinline__ void lw_update2(F2 &h, F2 &u, F2 &v, const Flux2 &Fl, const Flux2 &Fr, const Flux2 &Gd,
                                            const Flux2 &Gu, const Coef2 &k)
 {
-    h = fma2(k.ly, sub2(Gd.a, Gu.a), fma2(k.lx, sub2(Fl.a, Fr.a), h));
-    u = fma2(k.ly, sub2(Gd.b, Gu.b), fma2(k.lx, sub2(Fl.b, Fr.b), u));
-    v = fma2(k.ly, sub2(Gd.c, Gu.c), fma2(k.lx, sub2(Fl.c, Fr.c), v));
+    h = fma2(k.hy, sub2(Gd.a, Gu.a), fma2(k.hx, sub2(Fl.a, Fr.a), h));
+    u = fma2(k.hy, sub2(Gd.b, Gu.b), fma2(k.hx, sub2(Fl.b, Fr.b), u));
+    v = fma2(k.hy, sub2(Gd.c, Gu.c), fma2(k.hx, sub2(Fl.c, Fr.c), v));
 }
 
 // (lo of a, lo of b) and (hi of a, hi of b) style regroupings of fluxes

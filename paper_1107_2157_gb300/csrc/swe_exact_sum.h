@@ -15,9 +15,9 @@
 // exactly, and FP64 rounding enters only where flushed parts and the small
 // values are added to the total.
 //
-// Fast path: four values with the same sign and exponent bits, positive,
-// normal, finite and within 5 binades of R cost a few integer additions and
-// masks.  Each such group adds less than 4 * 2^24 * 2^5 = 2^31 units, so the
+// Fast path: four positive, normal, finite values whose exponents all lie in
+// [R - 5, R] (R >= 6) cost a few integer shifts, masks and additions.  Each
+// such group adds less than 4 * 2^24 * 2^5 = 2^31 units, so the
 // accumulator stays below 2^53 for up to 2^22 groups between flushes (a
 // thread of the mass kernel meets at most 2^12 for the largest grid, 65536^2
 // over 1024 blocks of 256 threads).
@@ -85,13 +85,17 @@ struct ExactSum32 {
     SWE_HD void add4(float x0, float x1, float x2, float x3)
     {
         const uint32_t b0 = f32_bits(x0), b1 = f32_bits(x1), b2 = f32_bits(x2), b3 = f32_bits(x3);
-        const uint32_t o = b0 | b1 | b2 | b3, a = b0 & b1 & b2 & b3;
-        const uint32_t E = a >> 23;  // the common sign and exponent bits, if any
-        const uint32_t d = (uint32_t)R - E;
-        if (((o ^ a) >> 23) == 0u && d <= 5u && E - 1u < 254u) {
-            const uint32_t s = (b0 & 0x7fffffu) + (b1 & 0x7fffffu) + (b2 & 0x7fffffu) + (b3 & 0x7fffffu) +
-                               4u * 0x800000u;
-            acc += (long long)(s << (5u - d));
+        // shift of each value's significand: its exponent - (R - 5), in [0, 5]
+        // on the fast path; a set sign bit or a larger exponent gives more
+        // than 5, a smaller exponent wraps around to a large unsigned value
+        const uint32_t base = (uint32_t)R - 5u;
+        const uint32_t s0 = (b0 >> 23) - base, s1 = (b1 >> 23) - base, s2 = (b2 >> 23) - base,
+                       s3 = (b3 >> 23) - base;
+        const uint32_t smax = s0 > s1 ? s0 : s1, smax2 = s2 > s3 ? s2 : s3;
+        if (R >= 6 && (smax > smax2 ? smax : smax2) <= 5u) {
+            const uint32_t s = (((b0 & 0x7fffffu) | 0x800000u) << s0) + (((b1 & 0x7fffffu) | 0x800000u) << s1) +
+                               (((b2 & 0x7fffffu) | 0x800000u) << s2) + (((b3 & 0x7fffffu) | 0x800000u) << s3);
+            acc += (long long)s;
         } else {
             add1(x0);
             add1(x1);

@@ -90,12 +90,7 @@ cudaError_t launch_packed(const CUtensorMap *map, void *out, int nx, int ny, lon
         attr = cudaFuncSetAttribute(lw_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPackedSmem);
     });
     if (attr != cudaSuccess) return attr;
-    Coef<float> k;
-    k.hx = (float)(0.5 * dt / dx);
-    k.hy = (float)(0.5 * dt / dy);
-    k.lx = (float)(dt / dx);
-    k.ly = (float)(dt / dy);
-    k.hg = (float)(0.5 * g);
+    const Coef<float> k = make_coef<float>(dx, dy, dt, g);
     const dim3 grid((nx + PackedCfg::TX - 1) / PackedCfg::TX, (ny + PackedCfg::TY - 1) / PackedCfg::TY);
     lw_packed_kernel<<<grid, 128, kPackedSmem, s>>>(*map, static_cast<float4 *>(out), nx, ny, ppitch, k, err);
     return cudaGetLastError();

@@ -14,6 +14,8 @@
 // rates, so the FP32 reductions keep FP64 operations off the per-cell path:
 // the mass sums FP32 depths exactly in 64-bit integers (ExactSum32) and the
 // CFL step screens cells with FP32 estimates before any FP64 evaluation.
+#include <algorithm>
+
 #include "swe_device.cuh"
 #include "swe_exact_sum.h"
 
@@ -22,10 +24,10 @@ namespace swe {
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
-size_t reduce_scratch_doubles() { return 5 * (size_t)kRedBlocks + 16; }
+size_t reduce_scratch_doubles() { return 5 * (size_t)kRedBlocks + 32; }
 
 // Scratch needed to reduce n grids with B blocks each.
-size_t reduce_scratch_doubles_many(int n, int B) { return 5 * (size_t)n * (size_t)B + 3 * (size_t)n + 16; }
+size_t reduce_scratch_doubles_many(int n, int B) { return 5 * (size_t)n * (size_t)B + 6 * (size_t)n + 16; }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -73,11 +75,61 @@ __device__ __forceinline__ RedGrid red_grid(const RedGrid &one, const RedGrid *_
     return one;
 }
 
+// Streams the 16-byte vectors of NP FP32 planes over the rows of block b
+// (rows b, b + B, ...; rows 16-byte aligned), Q vectors per thread and plane
+// per round.  The next round's loads are issued before the current round is
+// used, so the arithmetic runs under the memory latency.  f receives one
+// vector of each plane; the row tails (nx % 4 cells) are left to the caller.
+template <int NP, int Q, typename F>
+__device__ __forceinline__ void stream_rows4(const float *const (&P)[NP], long long pitch, int nx, int ny, int b,
+                                             int B, F &&f)
+{
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int nv = nx / 4, per_round = Q * T;
+    const int rpr = (nv + per_round - 1) / per_round;  // rounds per row
+    const int rows = b < ny ? (ny - 1 - b) / B + 1 : 0;
+    const int n = rows * rpr;
+    float4 A[NP][Q], Z[NP][Q];
+    auto load = [&](int i, float4(&buf)[NP][Q]) {
+        const int k = i / rpr, c = i - k * rpr;
+        const size_t ro = (size_t)(b + (size_t)k * B) * (size_t)pitch;
+        const int v0 = c * per_round + tid;
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int v = v0 + q * T;
+                buf[p][q] = v < nv ? __ldg(reinterpret_cast<const float4 *>(P[p] + ro) + v) : make_float4(0, 0, 0, 0);
+            }
+    };
+    auto use = [&](int i, const float4(&buf)[NP][Q]) {
+        const int v0 = (i % rpr) * per_round + tid;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (v0 + q * T >= nv) continue;
+            if constexpr (NP == 1)
+                f(buf[0][q]);
+            else
+                f(buf[0][q], buf[1][q], buf[2][q]);
+        }
+    };
+    if (n > 0) load(0, A);
+    int i = 0;
+    for (; i + 1 < n; i += 2) {
+        load(i + 1, Z);
+        use(i, A);
+        if (i + 2 < n) load(i + 2, A);
+        use(i + 1, Z);
+    }
+    if (i < n) use(i, A);
+}
+
 // Mass partials.  Each block takes rows blockIdx.x, blockIdx.x + gridDim.x,
 // ...; with VEC the threads read 16-byte vectors (4 FP32 / 2 FP64 values,
-// the row base and stride being 16-byte aligned), four per thread in flight,
-// and the row tail scalar.  FP32 depths are summed exactly (ExactSum32);
-// FP64 depths in two FP64 accumulators per thread.
+// the row base and stride being 16-byte aligned) -- FP32 through
+// stream_rows4, four per thread per round -- and the row tail scalar.  FP32
+// depths are summed exactly (ExactSum32); FP64 depths in two FP64
+// accumulators per thread.
 template <typename T, bool VEC, bool MANY>
 __global__ void __launch_bounds__(kRedThreads) mass_partial_kernel(RedGrid one, const RedGrid *__restrict__ many,
                                                                    double *partial)
@@ -88,10 +140,17 @@ __global__ void __launch_bounds__(kRedThreads) mass_partial_kernel(RedGrid one, 
     const T *H = static_cast<const T *>(G.h);
     double s0 = 0.0, s1 = 0.0;
     ExactSum32 ex;
+    if constexpr (F32 && VEC) {
+        const float *planes[1] = {static_cast<const float *>(G.h)};
+        stream_rows4<1, 4>(planes, G.pitch, G.nx, G.ny, blockIdx.x, gridDim.x,
+                           [&](const float4 &x) { ex.add4(x.x, x.y, x.z, x.w); });
+    }
     for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
         const T *row = H + (size_t)j * (size_t)G.pitch;
         int i0 = 0;
-        if (VEC) {
+        if (F32 && VEC) {
+            i0 = (G.nx / 4) * 4;
+        } else if (VEC) {
             const int nv = G.nx / N;
             for (int v0 = threadIdx.x; v0 < nv; v0 += 4 * blockDim.x) {
                 if constexpr (F32) {
@@ -154,9 +213,21 @@ __global__ void __launch_bounds__(1024) sum_final_kernel(RedGrid one, const RedG
 // meets the same (h, momentum) bits again, so flat regions cost one FP64
 // evaluation per thread.
 //
+// Pass 2 splits each block's rows into S column chunks, one CTA each, so
+// the few blocks that hold candidates are read by S CTAs in parallel; the
+// exact maxima meet in one slot per grid through an atomic maximum on their
+// bit patterns (non-negative doubles order as unsigned integers), which
+// gives the same result in any order.
+//
+// The blocks of a grid that hold candidates are listed by the pass-1 final
+// kernel, and pass 2 runs a fixed, small grid of CTAs over the items (listed
+// block, column chunk) of that list.
+//
 // Scratch layout for n grids of B blocks (P = n*B doubles per array):
 // [0,P) ax  [P,2P) ay  [2P,3P) bad  [3P,3P+3n) thresholds (thx, thy, bad)
-// [3P+3n, 4P+3n) exact sx partials  [4P+3n, 5P+3n) exact sy partials.
+// [3P+3n, 3P+5n) exact (sx, sy) maxima per grid
+// [3P+5n, 4P+5n) candidate blocks of each grid (B slots per grid)
+// [4P+5n, 4P+6n) the number of candidates of each grid.
 // ---------------------------------------------------------------------------
 constexpr float kCflSlack = 1.0f / 65536.0f;
 
@@ -181,19 +252,25 @@ __device__ __forceinline__ void cfl_estimate(float h, float u, float v, float g3
 // gridDim.x, ...) in the data's own type.  With VEC (FP32 planes, 16-byte
 // aligned rows) a thread loads two 16-byte vectors of each plane at a time
 // and takes the row tail one cell at a time.
+// ``b`` and ``B`` (the row blocks) replace blockIdx.x and gridDim.x, and the
+// visit covers column chunk ``sc`` of ``S`` equal chunks of each row.
 template <typename T, bool VEC, typename F>
-__device__ __forceinline__ void for_cells(const RedGrid &G, F &&f)
+__device__ __forceinline__ void for_cells(const RedGrid &G, F &&f, int b = -1, int B = 0, int sc = 0, int S = 1)
 {
     const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
-    for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+    if (b < 0) {
+        b = blockIdx.x;
+        B = gridDim.x;
+    }
+    for (int j = b; j < G.ny; j += B) {
         const size_t ro = (size_t)j * (size_t)G.pitch;
-        int i0 = 0;
         if constexpr (VEC && sizeof(T) == 4) {
             const float4 *h4 = reinterpret_cast<const float4 *>(H + ro);
             const float4 *u4 = reinterpret_cast<const float4 *>(U + ro);
             const float4 *v4 = reinterpret_cast<const float4 *>(V + ro);
-            const int nv = G.nx / 4;
-            for (int v0 = threadIdx.x; v0 < nv; v0 += 2 * blockDim.x) {
+            const int nv_all = G.nx / 4, cw = (nv_all + S - 1) / S;
+            const int nv = min(nv_all, (sc + 1) * cw);
+            for (int v0 = sc * cw + threadIdx.x; v0 < nv; v0 += 2 * blockDim.x) {
                 float4 a[2], b[2], c[2];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
@@ -214,9 +291,13 @@ __device__ __forceinline__ void for_cells(const RedGrid &G, F &&f)
                     }
                 }
             }
-            i0 = nv * 4;
+            if (sc == S - 1)
+                for (int i = nv_all * 4 + threadIdx.x; i < G.nx; i += blockDim.x) f(H[ro + i], U[ro + i], V[ro + i]);
+        } else {
+            const int cw = (G.nx + S - 1) / S;
+            const int i1 = min(G.nx, (sc + 1) * cw);
+            for (int i = sc * cw + threadIdx.x; i < i1; i += blockDim.x) f(H[ro + i], U[ro + i], V[ro + i]);
         }
-        for (int i = i0 + threadIdx.x; i < G.nx; i += blockDim.x) f(H[ro + i], U[ro + i], V[ro + i]);
     }
 }
 
@@ -228,7 +309,7 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(RedGrid one, con
     const size_t P = (size_t)gridDim.x * gridDim.y;
     float ax = 0.0f, ay = 0.0f;
     double bad = 0.0;
-    for_cells<T, VEC>(G, [&](T h, T u, T v) {
+    auto cell = [&](T h, T u, T v) {
         if (cell_bad<T>(h, u, v)) {
             bad += 1.0;
             return;
@@ -237,7 +318,25 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass1_kernel(RedGrid one, con
         cfl_estimate((float)h, (float)u, (float)v, g32, ex, ey);
         ax = fmaxf(ax, ex);
         ay = fmaxf(ay, ey);
-    });
+    };
+    if constexpr (VEC && sizeof(T) == 4) {
+        const float *planes[3] = {static_cast<const float *>(G.h), static_cast<const float *>(G.u),
+                                  static_cast<const float *>(G.v)};
+        stream_rows4<3, 2>(planes, G.pitch, G.nx, G.ny, blockIdx.x, gridDim.x,
+                           [&](const float4 &h, const float4 &u, const float4 &v) {
+                               cell(h.x, u.x, v.x);
+                               cell(h.y, u.y, v.y);
+                               cell(h.z, u.z, v.z);
+                               cell(h.w, u.w, v.w);
+                           });
+        const T *H = static_cast<const T *>(G.h), *U = static_cast<const T *>(G.u), *V = static_cast<const T *>(G.v);
+        for (int j = blockIdx.x; j < G.ny; j += gridDim.x) {
+            const size_t ro = (size_t)j * (size_t)G.pitch;
+            for (int i = (G.nx / 4) * 4 + threadIdx.x; i < G.nx; i += blockDim.x) cell(H[ro + i], U[ro + i], V[ro + i]);
+        }
+    } else {
+        for_cells<T, VEC>(G, cell);
+    }
     ax = (float)block_reduce<false, true>((double)ax);
     ay = (float)block_reduce<false, true>((double)ay);
     bad = block_reduce<false, false>(bad);
@@ -269,7 +368,22 @@ __global__ void __launch_bounds__(1024) cfl_pass1_final_kernel(double *scratch, 
         th[0] = (isfinite(ax) && ax > 1e-30) ? ax * (1.0 - (double)kCflSlack) : -1.0;
         th[1] = (isfinite(ay) && ay > 1e-30) ? ay * (1.0 - (double)kCflSlack) : -1.0;
         th[2] = bad;
+        double *ex = scratch + 3 * P + 3 * (size_t)n + 2 * (size_t)blockIdx.x;
+        ex[0] = 0.0;
+        ex[1] = 0.0;
     }
+    // the candidate list, with pass 2's screen: a block whose maxima lie
+    // below both FP32 thresholds holds no candidate
+    __shared__ int count;
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
+    const double *th = scratch + 3 * P + 3 * (size_t)blockIdx.x;
+    const float thx = __double2float_rd(th[0]), thy = __double2float_rd(th[1]);
+    double *list = scratch + 3 * P + 5 * (size_t)n + o;
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+        if (!((float)scratch[o + i] < thx && (float)scratch[P + o + i] < thy)) list[atomicAdd(&count, 1)] = (double)i;
+    __syncthreads();
+    if (threadIdx.x == 0) scratch[4 * P + 5 * (size_t)n + blockIdx.x] = (double)count;
 }
 
 // Exact FP64 sx or sy of one cell, every operation correctly rounded.
@@ -278,22 +392,26 @@ __device__ __forceinline__ double exact_speed(double g, double h, double m)
     return __dadd_rn(__dsqrt_rn(__dmul_rn(g, h)), fabs(__ddiv_rn(m, h)));
 }
 
-// Pass 2.  A block whose pass-1 maxima (same rows, same estimates) lie
-// below both thresholds holds no candidate and reads nothing.
+// Pass 2: the CTAs of grid blockIdx.y stride over the items (candidate
+// block, column chunk) of that grid's list: item i is chunk i % S of the
+// rows of listed block list[i / S].  Blocks not listed hold no candidate.
 template <typename T, bool VEC, bool MANY>
 __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, const RedGrid *__restrict__ many,
-                                                                float g32, double g, double *scratch)
+                                                                float g32, double g, double *scratch, int B, int S)
 {
     const RedGrid G = red_grid<MANY>(one, many);
     const size_t n = gridDim.y;
-    const size_t P = (size_t)gridDim.x * n;
-    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t P = (size_t)B * n;
     const double *th = scratch + 3 * P + 3 * (size_t)blockIdx.y;
+    const double *list = scratch + 3 * P + 5 * n + (size_t)blockIdx.y * B;
+    const int items = (int)scratch[4 * P + 5 * n + blockIdx.y] * S;
     // thresholds as floats rounded toward -inf: the screen keeps every
     // candidate the FP64 threshold keeps, and compares in FP32
     const float thx = __double2float_rd(th[0]), thy = __double2float_rd(th[1]);
     double sx = 0.0, sy = 0.0;
-    if (!((float)scratch[b] < thx && (float)scratch[P + b] < thy)) {
+    if ((int)blockIdx.x >= items) return;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int rb = (int)list[it / S], sc = it % S;
         T lhx = T(-1), lux = T(0), lhy = T(-1), lvy = T(0);  // last exactly evaluated inputs
         double lsx = 0.0, lsy = 0.0;
         for_cells<T, VEC>(G, [&](T h, T u, T v) {
@@ -316,13 +434,14 @@ __global__ void __launch_bounds__(kRedThreads) cfl_pass2_kernel(RedGrid one, con
                 }
                 sy = fmax(sy, lsy);
             }
-        });
-        sx = block_reduce<false, true>(sx);
-        sy = block_reduce<false, true>(sy);
+        }, rb, B, sc, S);
     }
+    sx = block_reduce<false, true>(sx);
+    sy = block_reduce<false, true>(sy);
     if (threadIdx.x == 0) {
-        scratch[3 * P + 3 * n + b] = sx;
-        scratch[4 * P + 3 * n + b] = sy;
+        unsigned long long *ex = reinterpret_cast<unsigned long long *>(scratch + 3 * P + 3 * n + 2 * (size_t)blockIdx.y);
+        atomicMax(ex, (unsigned long long)__double_as_longlong(sx));
+        atomicMax(ex + 1, (unsigned long long)__double_as_longlong(sy));
     }
 }
 
@@ -334,15 +453,9 @@ __global__ void __launch_bounds__(1024) cfl_final_kernel(RedGrid one, const RedG
 {
     const RedGrid G = MANY ? many[blockIdx.x] : one;
     const size_t P = (size_t)n * B;
-    const size_t o = (size_t)blockIdx.x * B;
-    double sx = 0.0, sy = 0.0;
-    for (int i = threadIdx.x; i < B; i += blockDim.x) {
-        sx = fmax(sx, scratch[3 * P + 3 * (size_t)n + o + i]);
-        sy = fmax(sy, scratch[4 * P + 3 * (size_t)n + o + i]);
-    }
-    sx = block_reduce<false, true>(sx);
-    sy = block_reduce<false, true>(sy);
     if (threadIdx.x == 0) {
+        const double sx = scratch[3 * P + 3 * (size_t)n + 2 * (size_t)blockIdx.x];
+        const double sy = scratch[3 * P + 3 * (size_t)n + 2 * (size_t)blockIdx.x + 1];
         const double tx = __ddiv_rn(G.dx, sx), ty = __ddiv_rn(G.dy, sy);
         out[2 * (size_t)blockIdx.x] = __dmul_rn(cfl, fmin(tx, ty));
         out[2 * (size_t)blockIdx.x + 1] = scratch[3 * P + 3 * (size_t)blockIdx.x + 2];
@@ -398,8 +511,12 @@ static void cfl_launch(const RedGrid &one, const RedGrid *many, int n, int B, do
     const float g32 = (float)g;
     cfl_pass1_kernel<T, VEC, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, scratch);
     cfl_pass1_final_kernel<<<n, 1024, 0, s>>>(scratch, n, B);
-    cfl_pass2_kernel<T, VEC, MANY><<<grid, kRedThreads, 0, s>>>(one, many, g32, g, scratch);
-    cfl_final_kernel<MANY><<<n, 1024, 0, s>>>(one, many, scratch, n, B, cfl, out);
+    // column chunks of about 1024 cells (at most 8) for a single grid; a
+    // fixed grid of CTAs per reduced grid strides over the candidate items
+    const int S = MANY ? 1 : std::max(1, std::min(8, one.nx / 1024));
+    const int ctas = MANY ? 8 : 256;
+    cfl_pass2_kernel<T, VEC, MANY><<<dim3(ctas, n), kRedThreads, 0, s>>>(one, many, g32, g, scratch, B, S);
+    cfl_final_kernel<MANY><<<n, 32, 0, s>>>(one, many, scratch, n, B, cfl, out);
 }
 
 cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, int nx, int ny, long long pitch,

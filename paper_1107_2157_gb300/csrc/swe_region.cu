@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(S::NT) region_lw_kernel(const __grid_constant_
 
 __global__ void div_probe_kernel(const float *a, const float *b, float *out, int n, int which)
 {
+    if (which == 4) {  // the stencil kernels' approximate reciprocal
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = rcp(b[i]);
+        return;
+    }
     if (which == 3) {  // the fast division's reciprocal step alone
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
             out[i] = rcp_rn_fast(b[i]);
@@ -621,7 +625,7 @@ swe_status swe_region_query(swe_region *r, int key, long long *value)
 
 swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, int which, void *stream)
 {
-    if (!a || !b || !out || n < 0 || which < 0 || which > 3 || (which == 2 && n % 2)) return SWE_EINVAL;
+    if (!a || !b || !out || n < 0 || which < 0 || which > 4 || (which == 2 && n % 2)) return SWE_EINVAL;
     if (n == 0) return SWE_OK;
     div_probe_kernel<<<std::min((n + 255) / 256, 4096), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, b, out, n,
                                                                                                        which);

@@ -19,17 +19,6 @@
 
 namespace swe {
 
-template <typename T>
-static Coef<T> make_coef(double dx, double dy, double dt, double g)
-{
-    Coef<T> k;
-    k.hx = (T)(0.5 * dt / dx);
-    k.hy = (T)(0.5 * dt / dy);
-    k.lx = (T)(dt / dx);
-    k.ly = (T)(dt / dy);
-    k.hg = (T)(0.5 * g);
-    return k;
-}
 
 // ---------------------------------------------------------------------------
 // Naive kernel

@@ -138,21 +138,13 @@ __device__ __forceinline__ void strip_compute_pairs(const Box &box, int BW, int 
 {
     auto sidx = [&](int c, int r) { return (r + row_off) * BW + c + AX; };
     const Coef2 k2 = coef2(k);
-    CellQ2 cur[2], nxt[2];
-    Flux2 gd[2], gu[2];
+    CellQ2 ca[2], cb[2];
+    Flux2 ga[2], gb[2];
 
-    box.row2(sidx(cx, r_begin), k2, cur);
-    if (!GHOSTED && y0 + r_begin == 0) {
-        nxt[0] = mirror_y2(cur[0]);
-        nxt[1] = mirror_y2(cur[1]);
-    } else {
-        box.row2(sidx(cx, r_begin - 1), k2, nxt);
-    }
-    gd[0] = yface_flux2(nxt[0], cur[0], k2);
-    gd[1] = yface_flux2(nxt[1], cur[1], k2);
-
-#pragma unroll 1
-    for (int r = r_begin; r < r_end; ++r) {
+    // One row: ``cur`` holds row r and ``gd`` its lower y-faces; row r + 1
+    // goes to ``nxt`` and the faces between them to ``gu``.  The loop below
+    // alternates the roles of the two sets, so nothing is copied per row.
+    auto row = [&](int r, CellQ2(&cur)[2], CellQ2(&nxt)[2], const Flux2(&gd)[2], Flux2(&gu)[2]) {
         if (!GHOSTED && y0 + r + 1 == ny) {
             nxt[0] = mirror_y2(cur[0]);
             nxt[1] = mirror_y2(cur[1]);
@@ -183,11 +175,25 @@ __device__ __forceinline__ void strip_compute_pairs(const Box &box, int BW, int 
         unpack2(ov0, ov[0], ov[1]);
         unpack2(ov1, ov[2], ov[3]);
         store(r, oh, ou, ov);
-        cur[0] = nxt[0];
-        cur[1] = nxt[1];
-        gd[0] = gu[0];
-        gd[1] = gu[1];
+    };
+
+    box.row2(sidx(cx, r_begin), k2, ca);
+    if (!GHOSTED && y0 + r_begin == 0) {
+        cb[0] = mirror_y2(ca[0]);
+        cb[1] = mirror_y2(ca[1]);
+    } else {
+        box.row2(sidx(cx, r_begin - 1), k2, cb);
     }
+    ga[0] = yface_flux2(cb[0], ca[0], k2);
+    ga[1] = yface_flux2(cb[1], ca[1], k2);
+
+    int r = r_begin;
+#pragma unroll 1
+    for (; r + 1 < r_end; r += 2) {
+        row(r, ca, cb, ga, gb);
+        row(r + 1, cb, ca, gb, ga);
+    }
+    if (r < r_end) row(r, ca, cb, ga, gb);
 }
 
 template <typename T, int VX, bool XEDGE, typename Box, typename Store, bool GHOSTED = false>
@@ -372,50 +378,65 @@ struct Tb2Cfg {
     static constexpr size_t SMEM = 3 * IN_STRIDE + 3 * C::BOX_STRIDE + 128;
 };
 
+// Phase 1: the intermediate state on rows [-1, TY] of the tile's columns
+// (the ring rows included) into the intermediate box, cut among the lane
+// groups as phase 2 cuts them, so phase 2 finds every cell inside the grid
+// that it reads here or in the ring columns.  All threads of the CTA call it.
+template <typename T, int NWARP, int RY>
+__device__ __forceinline__ void tb2_phase1(const T *iH, const T *iU, const T *iV, T *mH_, T *mU_, T *mV_, int nx,
+                                           int ny, int x0, int y0, const Coef<T> &k)
+{
+    using C = TiledCfg<T, NWARP, RY>;
+    constexpr int VX = C::VX;
+    const bool xedge = (x0 == 0) || (x0 + C::TX >= nx);
+    const TileWork tw = tile_work<C::TX, VX, NWARP>(xedge, x0, nx, max(-1, -y0), min(C::TY + 1, ny - y0));
+    const int cx = tw.cx, gx = x0 + cx, r0 = tw.rb, r1 = tw.re;
+    auto to_mid = [&](int r, const T(&h)[VX], const T(&u)[VX], const T(&v)[VX]) {
+        const int o = (r + 1) * C::BW + cx + C::AX;
+        store_vec<T, VX>(mH_ + o, h);
+        store_vec<T, VX>(mU_ + o, u);
+        store_vec<T, VX>(mV_ + o, v);
+    };
+    if (xedge)
+        strip_compute<T, VX, true>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
+    else
+        strip_compute<T, VX, false>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
+    // the ring columns -1 and TX, one cell at a time
+    for (int idx = threadIdx.x; idx < 2 * (C::TY + 2); idx += blockDim.x) {
+        const int c = (idx & 1) ? C::TX : -1;
+        const int r = (idx >> 1) - 1;
+        const int cgx = x0 + c, gy = y0 + r;
+        if (cgx < 0 || cgx >= nx || gy < 0 || gy >= ny) continue;
+        T h, hu, hv;
+        box_cell<T>(iH, iU, iV, C::BW, C::AX, 2, c, r, cgx, gy, nx, ny, k, h, hu, hv);
+        const int o = (r + 1) * C::BW + c + C::AX;
+        mH_[o] = h;
+        mU_[o] = hu;
+        mV_[o] = hv;
+    }
+}
+
+// Phase 2: the second step from the intermediate box to global memory.
+// Returns true if some stored depth is not positive.
+template <typename T, int NWARP, int RY>
+__device__ __forceinline__ bool tb2_phase2(const T *mH_, const T *mU_, const T *mV_, T *__restrict__ oH,
+                                           T *__restrict__ oU, T *__restrict__ oV, int nx, int ny, long long pitch,
+                                           int x0, int y0, const Coef<T> &k)
+{
+    using C = TiledCfg<T, NWARP, RY>;
+    const bool xedge = (x0 == 0) || (x0 + C::TX >= nx);
+    if (xedge) return tiled_compute<T, NWARP, RY, true>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
+    return tiled_compute<T, NWARP, RY, false>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
+}
+
 template <typename T, int NWARP, int RY>
 __device__ __forceinline__ bool tb2_tile_compute(const T *iH, const T *iU, const T *iV, T *mH_, T *mU_, T *mV_,
                                                  T *__restrict__ oH, T *__restrict__ oU, T *__restrict__ oV,
                                                  int nx, int ny, long long pitch, int x0, int y0, const Coef<T> &k)
 {
-    using C = TiledCfg<T, NWARP, RY>;
-    constexpr int VX = C::VX;
-    const bool xedge = (x0 == 0) || (x0 + C::TX >= nx);
-
-    // phase 1: intermediate state on rows [-1, TY] of the tile's columns (the
-    // ring rows included), cut among the lane groups as phase 2 cuts them, so
-    // phase 2 finds every cell inside the grid that it reads here or in the
-    // ring columns
-    {
-        const TileWork tw = tile_work<C::TX, VX, NWARP>(xedge, x0, nx, max(-1, -y0), min(C::TY + 1, ny - y0));
-        const int cx = tw.cx, gx = x0 + cx, r0 = tw.rb, r1 = tw.re;
-        auto to_mid = [&](int r, const T(&h)[VX], const T(&u)[VX], const T(&v)[VX]) {
-            const int o = (r + 1) * C::BW + cx + C::AX;
-            store_vec<T, VX>(mH_ + o, h);
-            store_vec<T, VX>(mU_ + o, u);
-            store_vec<T, VX>(mV_ + o, v);
-        };
-        if (xedge)
-            strip_compute<T, VX, true>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
-        else
-            strip_compute<T, VX, false>(iH, iU, iV, C::BW, C::AX, 2, r0, r1, cx, gx, nx, ny, y0, k, to_mid);
-        // the ring columns -1 and TX, one cell at a time
-        for (int idx = threadIdx.x; idx < 2 * (C::TY + 2); idx += blockDim.x) {
-            const int c = (idx & 1) ? C::TX : -1;
-            const int r = (idx >> 1) - 1;
-            const int cgx = x0 + c, gy = y0 + r;
-            if (cgx < 0 || cgx >= nx || gy < 0 || gy >= ny) continue;
-            T h, hu, hv;
-            box_cell<T>(iH, iU, iV, C::BW, C::AX, 2, c, r, cgx, gy, nx, ny, k, h, hu, hv);
-            const int o = (r + 1) * C::BW + c + C::AX;
-            mH_[o] = h;
-            mU_[o] = hu;
-            mV_[o] = hv;
-        }
-    }
+    tb2_phase1<T, NWARP, RY>(iH, iU, iV, mH_, mU_, mV_, nx, ny, x0, y0, k);
     __syncthreads();
-    // phase 2: the second step from the intermediate box to global memory
-    if (xedge) return tiled_compute<T, NWARP, RY, true>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
-    return tiled_compute<T, NWARP, RY, false>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
+    return tb2_phase2<T, NWARP, RY>(mH_, mU_, mV_, oH, oU, oV, nx, ny, pitch, x0, y0, k);
 }
 
 }  // namespace swe

@@ -396,3 +396,48 @@ def test_narrow_edge_tiles_equal_the_naive_kernel(dtype):
             got = run_gpu(s, 1.0, 1.0, dt, G, 7, dtype, kernel)
             for k in range(3):
                 assert np.array_equal(got[k], ref[k]), (nx, ny, kernel, k)
+
+
+def test_stencil_reciprocal_halves_when_its_argument_doubles():
+    """The flux functions carry face states doubled (Coef in swe_device.cuh)
+    and so rely on rcp(2x) = rcp(x) / 2 for the approximate FP32 reciprocal
+    (exact for IEEE division).  Every significand of the binades of depths
+    from 2^-8 to 2^16, each against the next binade, bit for bit; and the
+    reciprocal stays within its documented one-ulp bound of the host's 1/x."""
+    import torch
+    from paper_1107_2157_gb300 import swe
+    sig = np.arange(1 << 23, dtype=np.uint32)
+    for e in (-8, -1, 0, 1, 3, 15):
+        x = ((np.uint32(127 + e) << np.uint32(23)) | sig).view(np.float32)
+        both = np.concatenate([x, 2 * x]).astype(np.float32)
+        bd = torch.from_numpy(both).cuda()
+        o = torch.empty_like(bd)
+        swe.check(swe.lib().swe_selftest_div(bd.data_ptr(), bd.data_ptr(), o.data_ptr(), both.size, 4,
+                                             swe.current_stream()), "swe_selftest_div")
+        got = o.cpu().numpy()
+        r1, r2 = got[:x.size], got[x.size:]
+        bad = np.flatnonzero((0.5 * r1).view(np.uint32) != r2.view(np.uint32))
+        assert bad.size == 0, (e, bad[:5], x[bad[:5]], r1[bad[:5]], r2[bad[:5]])
+        exact = 1.0 / x.astype(np.float64)
+        ulp = np.spacing(exact.astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(r1 - exact) <= ulp), e
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_every_two_step_shape_equals_the_one_step_kernel_bitwise(variant):
+    """Shapes 0..3 take one CTA per tile, shape 4 (the FP32 default) runs
+    persistent CTAs that prefetch their next tile: all give the one-step
+    kernel's bits, on a grid with more tiles than resident CTAs' first pass
+    covers and ragged edges, and an odd step count."""
+    from paper_1107_2157_gb300 import Grid
+    nx, ny, steps = 1411, 777, 7
+    s = si.smooth_flow_state(4321, nx, ny).rounded_to(np.float32)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 0.9, 1.1, G, 0.3)
+    ref = run_gpu(s, 0.9, 1.1, dt, G, steps, "f32", KERNELS["tiled"])
+    with Grid(nx, ny, 0.9, 1.1, dt, G, dtype="f32", kernel=3, variant=variant) as grid:
+        grid.set_state(*(np.ascontiguousarray(a, np.float32) for a in (s.h, s.hu, s.hv)))
+        grid.step(steps)
+        got = grid.get_state()
+        assert grid.check() == 0
+    for k in range(3):
+        assert np.array_equal(got[k], ref[k]), (variant, k)
