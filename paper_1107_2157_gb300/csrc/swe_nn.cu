@@ -19,7 +19,8 @@
 // output row; the epilogue reads TMEM with tcgen05.ld and applies bias,
 // GELU, the loss or the GELU derivative.  Forward layers and the input
 // gradients (transposed convolutions with flipped, transposed weights) all
-// use this kernel.  Weight gradients are reduced on CUDA cores.
+// use this kernel.  Weight gradients run on the tensor cores too
+// (wgrad_tc_kernel, pixels as the MMA's K).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -275,6 +276,169 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
+// Weight gradients on the tensor cores.  dW[ky][kx][ci][co] = sum_p
+// X[p + (ky-1, kx-1)][ci] dY[p][co] is a GEMM with the pixels as K: both
+// activations are row-chunked, so for one image row a strip holds pixels at
+// a 16-byte stride with 8 channels contiguous in each -- a 16-bit MN-major
+// operand whose core matrices (8 channels x 8 pixels, 128 contiguous bytes)
+// lie 128 bytes apart along K and one strip (2080 bytes) apart along M or N.
+// In the staged box [rows][CHX][130][8] the strips of consecutive rows
+// continue at that same stride, so the 16 core-matrix groups of an M = 128
+// operand starting at output row r are (dy, strip) = (g / CHX, g % CHX),
+// dy = 0 .. 16/CHX - 1: one MMA covers the three vertical taps at once (the
+// groups with dy > 2 are computed and discarded).  The horizontal tap kx is
+// a 16-byte shift of the A start address, and each kx has its own TMEM
+// accumulator of N = COUT columns.
+//
+// wgrad_tc_kernel: persistent CTAs stride over tiles of 128 pixels x R rows
+// of one image; per tile thread 0 issues R x 3 x 8 MMAs (M = 128, N = 8 CHY,
+// K = 16 pixels, A and B MN-major) while all threads add the staged output
+// gradient into the bias gradient; at the end the accumulators go to the
+// CTA's partial row (the layout of the CUDA-core kernel's rows), which
+// reduce_rows_kernel sums in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kWgRows = 4;  // output rows per tile
+
+template <int CHX, int CHY>
+struct WgCfg {
+    static constexpr int N = 8 * CHY;                 // MMA N: output-gradient channels (padded)
+    static constexpr int DY = 16 / CHX;               // vertical taps one M = 128 operand spans
+    static constexpr int XROWS = kWgRows + DY - 1;    // staged input rows
+    static constexpr size_t X_BYTES = (size_t)XROWS * CHX * kStripB;
+    static constexpr size_t Y_BYTES = (size_t)kWgRows * CHY * kStripB;
+    static constexpr size_t OFF_Y = al128(X_BYTES);
+    static constexpr size_t OFF_RED = al128(OFF_Y + Y_BYTES);
+    static constexpr size_t OFF_BAR = al128(OFF_RED + (size_t)4 * 32 * 4);  // 4 warps x 32 bias partials
+    static constexpr size_t SMEM = OFF_BAR + 64 + 128;
+    static constexpr uint32_t TMEM_COLS = pow2_at_least((uint32_t)(3 * N));
+};
+
+template <int CHX, int CHY, int CIN, int COUT>
+__global__ void __launch_bounds__(128) wgrad_tc_kernel(const __grid_constant__ CUtensorMap mX,
+                                                       const __grid_constant__ CUtensorMap mY, int W, int H, int n,
+                                                       float *__restrict__ partial, int *err)
+{
+    using C = WgCfg<CHX, CHY>;
+    constexpr int N = C::N;
+    constexpr int NOUT = 9 * CIN * COUT + COUT;
+    static_assert(CIN <= 8 * CHX && COUT <= N && C::DY >= 3, "tile shape");
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sX = smem;
+    unsigned char *sY = smem + C::OFF_Y;
+    float *red = reinterpret_cast<float *>(smem + C::OFF_RED);
+    uint64_t *bar_tma = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    uint64_t *bar_mma = bar_tma + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_tma + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (W + kTileX - 1) / kTileX, tiles_y = (H + kWgRows - 1) / kWgRows;
+    const long long ntiles = (long long)tiles_x * tiles_y * n;
+
+    if (tid == 0) {
+        mbar_init(bar_tma, 1);
+        mbar_init(bar_mma, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, C::TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    float bacc[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bacc[c] = 0.0f;
+    constexpr uint32_t idesc = tc::idesc_bf16(128, N) | (1u << 15) | (1u << 16);  // A and B MN-major
+    bool ok = true, any = false;
+    uint32_t phase = 0;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, phase ^= 1u) {
+        const int tx = (int)(tile % tiles_x);
+        const int ty = (int)((tile / tiles_x) % tiles_y);
+        const int img = (int)(tile / ((long long)tiles_x * tiles_y));
+        const int x0 = tx * kTileX, y0 = ty * kWgRows;
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar_tma, (uint32_t)(C::X_BYTES + C::Y_BYTES));
+            tma_load_5d(sX, &mX, bar_tma, 0, x0 - 1, 0, y0 - 1, img);
+            tma_load_5d(sY, &mY, bar_tma, 0, x0, 0, y0, img);
+        }
+        ok = __syncthreads_and(mbar_wait_bounded(bar_tma, phase, err));
+        if (!ok) break;
+        tc::fence_after_sync();
+        if (tid == 0) {
+#pragma unroll 1
+            for (int r = 0; r < kWgRows; ++r) {
+#pragma unroll 1
+                for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks) {
+                        const unsigned char *a = sX + (size_t)r * CHX * kStripB + (size_t)(16 * ks + kx) * kPixB;
+                        const unsigned char *b = sY + (size_t)r * CHY * kStripB + (size_t)(16 * ks) * kPixB;
+                        tc::mma_bf16(tmem + (uint32_t)(kx * N), tc::smem_desc(a, 128, kStripB),
+                                     tc::smem_desc(b, 128, kStripB), idesc, any || r > 0 || ks > 0);
+                    }
+                }
+            }
+            tc::commit(bar_mma);
+        }
+        any = true;
+        // bias gradient: thread t adds pixel t of every staged row
+        {
+#pragma unroll
+            for (int r = 0; r < kWgRows; ++r) {
+#pragma unroll
+                for (int c8 = 0; c8 < (COUT + 7) / 8; ++c8) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(sY + ((size_t)r * CHY + c8) * kStripB +
+                                                                     (size_t)tid * kPixB);
+                    const bf16 *v = reinterpret_cast<const bf16 *>(&q);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (8 * c8 + k < COUT) bacc[8 * c8 + k] += __bfloat162float(v[k]);
+                }
+            }
+        }
+        fence_proxy_async_smem();  // the generic reads above come before the next TMA write
+        ok = mbar_wait_bounded(bar_mma, phase, err);
+        ok = __syncthreads_and(ok);
+        tc::fence_after_sync();
+    }
+
+    float *out = partial + (size_t)blockIdx.x * NOUT;
+    // bias: warp sums, then warp 0 adds the four warps' values in order
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) {
+        float v = bacc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp * 32 + c] = v;
+    }
+    __syncthreads();
+    if (tid < COUT) out[9 * CIN * COUT + tid] = ok ? ((red[tid] + red[32 + tid]) + red[64 + tid]) + red[96 + tid] : 0.0f;
+    // weights: TMEM lane m = row (dy, strip, channel) of the M = 128 operand
+    const int g = (warp * 32 + lane) >> 3, ky = g / CHX, ci = (g % CHX) * 8 + (lane & 7);
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx) {
+        float v[N];
+        if (any && ok) {
+            if constexpr (N == 32)
+                tc::ld_x32(tbase + (uint32_t)(kx * N), v);
+            else
+                tc::ld_x16(tbase + (uint32_t)(kx * N), v);
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] = 0.0f;
+        }
+        if (ky < 3 && ci < CIN) {
+            float *o = out + (size_t)((ky * 3 + kx) * CIN + ci) * COUT;
+#pragma unroll
+            for (int c = 0; c < COUT; ++c) o[c] = v[c];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, C::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
 // Small element-wise kernels
 // ---------------------------------------------------------------------------
 
@@ -371,94 +535,6 @@ __global__ void resample_kernel(const float *__restrict__ src, long long s_img, 
         }
         dst[i * d_img + f * d_plane + (long long)Y * d_pitch + X] = (float)(acc / (fx * fy));
     }
-}
-
-// Weight gradients on CUDA cores.  dW[t][ci][co] = sum_p X[p + d(t)][ci] dY[p][co],
-// db[co] = sum_p dY[p][co], over all pixels of all images.  A CTA takes
-// 32 x 8 pixel tiles (grid-stride), stages the input halo [10][ci][34] and the
-// output gradient [8][32][co] as floats, and each thread accumulates the 9
-// taps of its (ci, co) pairs in registers; one partial row per CTA.
-constexpr int kWgTx = 32, kWgTy = 8, kWgThreads = 512;
-
-template <int CHX, int CHY, int CIN, int COUT>
-__global__ void __launch_bounds__(kWgThreads) wgrad_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dY,
-                                                           int W, int H, int n, float *__restrict__ partial)
-{
-    constexpr int CX = CHX * 8, CY = CHY * 8;
-    constexpr int P = CIN * COUT;
-    constexpr int PPT = (P + kWgThreads - 1) / kWgThreads;
-    constexpr int NOUT = 9 * CIN * COUT + COUT;
-    extern __shared__ __align__(16) float wg_smem[];
-    float (*sX)[CIN][kWgTx + 2] = reinterpret_cast<float (*)[CIN][kWgTx + 2]>(wg_smem);
-    float (*sY)[kWgTx][COUT] =
-        reinterpret_cast<float (*)[kWgTx][COUT]>(wg_smem + (kWgTy + 2) * CIN * (kWgTx + 2));
-    float acc[PPT][9];
-    float bacc = 0.0f;
-#pragma unroll
-    for (int q = 0; q < PPT; ++q)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) acc[q][t] = 0.0f;
-    const int tid = threadIdx.x;
-    const int tiles_x = (W + kWgTx - 1) / kWgTx, tiles_y = (H + kWgTy - 1) / kWgTy;
-    const long long ntiles = (long long)tiles_x * tiles_y * n;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx = (int)(tile % tiles_x);
-        const int ty = (int)((tile / tiles_x) % tiles_y);
-        const int img = (int)(tile / ((long long)tiles_x * tiles_y));
-        const int x0 = tx * kWgTx, y0 = ty * kWgTy;
-        __syncthreads();
-        for (int e = tid; e < (kWgTy + 2) * (kWgTx + 2) * CIN; e += kWgThreads) {
-            const int px = e % (kWgTx + 2);
-            const int c = (e / (kWgTx + 2)) % CIN;
-            const int ry = e / ((kWgTx + 2) * CIN);
-            const int gx = x0 + px - 1, gy = y0 + ry - 1;
-            float v = 0.0f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H)
-                v = __bfloat162float(X[rc_index(img, gy, c / 8, gx, H, W, CHX) + (c % 8)]);
-            sX[ry][c][px] = v;
-        }
-        for (int e = tid; e < kWgTy * kWgTx * COUT; e += kWgThreads) {
-            const int c = e % COUT;
-            const int px = (e / COUT) % kWgTx;
-            const int ry = e / (COUT * kWgTx);
-            const int gx = x0 + px, gy = y0 + ry;
-            float v = 0.0f;
-            if (gx < W && gy < H) v = __bfloat162float(dY[rc_index(img, gy, c / 8, gx, H, W, CHY) + (c % 8)]);
-            sY[ry][px][c] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const int pr = tid + q * kWgThreads;
-            if (pr < P) {
-                const int ci = pr / COUT, co = pr % COUT;
-#pragma unroll 1
-                for (int ry = 0; ry < kWgTy; ++ry)
-#pragma unroll 2
-                    for (int px = 0; px < kWgTx; ++px) {
-                        const float y = sY[ry][px][co];
-#pragma unroll
-                        for (int t = 0; t < 9; ++t) acc[q][t] += sX[ry + t / 3][ci][px + t % 3] * y;
-                    }
-            }
-        }
-        if (tid < COUT)
-            for (int ry = 0; ry < kWgTy; ++ry)
-                for (int px = 0; px < kWgTx; ++px) bacc += sY[ry][px][tid];
-    }
-    (void)CX;
-    (void)CY;
-    float *out = partial + (size_t)blockIdx.x * NOUT;
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        const int pr = tid + q * kWgThreads;
-        if (pr < P) {
-            const int ci = pr / COUT, co = pr % COUT;
-#pragma unroll
-            for (int t = 0; t < 9; ++t) out[(t * CIN + ci) * COUT + co] = acc[q][t];
-        }
-    }
-    if (tid < COUT) out[9 * CIN * COUT + tid] = bacc;
 }
 
 // Sums the per-CTA partial rows in a fixed order: grad[j] = sum_b partial[b][j].
@@ -664,18 +740,18 @@ cudaError_t launch_conv(const CUtensorMap &map, const bf16 *wimg, const EpiArgs 
 }
 
 template <int CHX, int CHY, int CIN, int COUT>
-cudaError_t launch_wgrad(const bf16 *X, const bf16 *dY, int W, int H, int n, float *partial, float *grad_w,
-                         float *grad_b, cudaStream_t s)
+cudaError_t launch_wgrad(const CUtensorMap &mX, const CUtensorMap &mY, int W, int H, int n, float *partial,
+                         float *grad_w, float *grad_b, int *err, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(float) * ((kWgTy + 2) * CIN * (kWgTx + 2) + kWgTy * kWgTx * COUT);
-    auto kern = wgrad_kernel<CHX, CHY, CIN, COUT>;
+    using C = WgCfg<CHX, CHY>;
+    auto kern = wgrad_tc_kernel<CHX, CHY, CIN, COUT>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [&] { attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
+    std::call_once(once, [&] { attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); });
     if (attr != cudaSuccess) return attr;
-    const long long ntiles = (long long)((W + kWgTx - 1) / kWgTx) * ((H + kWgTy - 1) / kWgTy) * n;
+    const long long ntiles = (long long)((W + kTileX - 1) / kTileX) * ((H + kWgRows - 1) / kWgRows) * n;
     const int blocks = (int)std::min<long long>(ntiles, kWgBlocks);
-    kern<<<blocks, kWgThreads, smem, s>>>(X, dY, W, H, n, partial);
+    kern<<<blocks, 128, C::SMEM, s>>>(mX, mY, W, H, n, partial, err);
     constexpr int nw = 9 * CIN * COUT;
     reduce_rows_kernel<<<(nw + COUT + 255) / 256, 256, 0, s>>>(partial, blocks, nw + COUT, grad_w);
     // the bias part of each row sits right after the weights: copy it to grad_b
@@ -696,6 +772,7 @@ struct swe_net {
          *dz1 = nullptr;
     float *resid = nullptr;
     CUtensorMap m_x0, m_a1, m_a2, m_dr, m_dz2;
+    CUtensorMap g_x0, g_a1, g_a2, g_dr, g_dz2, g_dz1;  // boxes of the weight-gradient kernel
     float norm[5] = {1.0f, 1.0f, 1.0f, 1.0f, 1.0f};  // h0, sh, su, oh, ou
     double *loss = nullptr, *h_loss = nullptr;
     double *hsum = nullptr;
@@ -805,7 +882,13 @@ swe_status swe_net_create(int max_images, int H, int W, swe_net **out)
         !encode_act_map(&t->m_a1, t->a1, W, H, 4, max_images, rows) ||
         !encode_act_map(&t->m_a2, t->a2, W, H, 4, max_images, rows) ||
         !encode_act_map(&t->m_dr, t->dr, W, H, 2, max_images, rows) ||
-        !encode_act_map(&t->m_dz2, t->dz2, W, H, 4, max_images, rows))
+        !encode_act_map(&t->m_dz2, t->dz2, W, H, 4, max_images, rows) ||
+        !encode_act_map(&t->g_x0, t->x0, W, H, 2, max_images, WgCfg<2, 4>::XROWS) ||
+        !encode_act_map(&t->g_a1, t->a1, W, H, 4, max_images, WgCfg<4, 4>::XROWS) ||
+        !encode_act_map(&t->g_a2, t->a2, W, H, 4, max_images, WgCfg<4, 2>::XROWS) ||
+        !encode_act_map(&t->g_dr, t->dr, W, H, 2, max_images, kWgRows) ||
+        !encode_act_map(&t->g_dz2, t->dz2, W, H, 4, max_images, kWgRows) ||
+        !encode_act_map(&t->g_dz1, t->dz1, W, H, 4, max_images, kWgRows))
         return fail(SWE_ECUDA);
     *out = t;
     return SWE_OK;
@@ -960,11 +1043,11 @@ swe_status swe_net_train_step(swe_net *t, int n, const float *target, float lr, 
     b2.zin = t->z1;
     N_TRY((launch_conv<4, 32, EPI_GELU_BWD>(t->m_dz2, t->w2d, b2, W, H, n, t->err, s)));
     // weight gradients
-    N_TRY((launch_wgrad<4, 2, 32, 3>(t->a2, t->dr, W, H, n, t->partial, t->grads + kOffW3, t->gtmp, s)));
+    N_TRY((launch_wgrad<4, 2, 32, 3>(t->g_a2, t->g_dr, W, H, n, t->partial, t->grads + kOffW3, t->gtmp, t->err, s)));
     N_TRY(cudaMemcpyAsync(t->grads + kOffB3, t->gtmp, 3 * 4, cudaMemcpyDeviceToDevice, s));
-    N_TRY((launch_wgrad<4, 4, 32, 32>(t->a1, t->dz2, W, H, n, t->partial, t->grads + kOffW2, t->gtmp, s)));
+    N_TRY((launch_wgrad<4, 4, 32, 32>(t->g_a1, t->g_dz2, W, H, n, t->partial, t->grads + kOffW2, t->gtmp, t->err, s)));
     N_TRY(cudaMemcpyAsync(t->grads + kOffB2, t->gtmp, 32 * 4, cudaMemcpyDeviceToDevice, s));
-    N_TRY((launch_wgrad<2, 4, 3, 32>(t->x0, t->dz1, W, H, n, t->partial, t->grads + kOffW1, t->gtmp, s)));
+    N_TRY((launch_wgrad<2, 4, 3, 32>(t->g_x0, t->g_dz1, W, H, n, t->partial, t->grads + kOffW1, t->gtmp, t->err, s)));
     N_TRY(cudaMemcpyAsync(t->grads + kOffB1, t->gtmp, 32 * 4, cudaMemcpyDeviceToDevice, s));
     if (update) {
         t->step += 1;
