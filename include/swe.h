@@ -70,7 +70,9 @@ typedef struct {
     int dtype;   /* swe_dtype; default SWE_F32 */
     int kernel;  /* swe_kernel; default SWE_KERNEL_AUTO */
     int depth;   /* 0 = default; SWE_KERNEL_TEMPORAL runs 2 steps per launch */
-    int reserved[5]; /* reserved[0]: two-step tile shape + 1 (0 = default shape 1 of 0..3); others 0 */
+    int reserved[5]; /* reserved[0]: two-step kernel shape + 1 (0 = the default, shape 4); shapes 0..3 take
+                        one CTA per tile (warps x rows: 4x8, 8x4, 4x4, 8x2), shape 4 is 8x4 with persistent
+                        CTAs that prefetch their next tile; others 0 */
 } swe_options;
 
 /* Fills *opt with the defaults (FP32, automatic kernel choice). */
@@ -339,6 +341,32 @@ typedef enum {
 } swe_part_query_key;
 swe_status swe_part_query(swe_part *part, int key, long long *value);
 
+/*
+ * One rank's partition of a grid decomposed across processes (Sec. 4.1 and
+ * Fig. 1: each MPI rank holds its part of the global array with a halo).
+ * swe_part_create_rank makes a single nx x ny partition whose sides in the
+ * bitmask ``walls`` (1 left, 2 right, 4 bottom, 8 top) lie on the global
+ * boundary: their ghosts are filled by swe_part_step as reflective walls.
+ * The ghosts of the other sides face another rank's partition; before each
+ * swe_part_step the caller writes them with swe_part_set_ghosts from that
+ * rank's edge cells, which swe_part_edges reads.  Both use one device
+ * buffer of 6 (nx + ny) floats, the four sides' strips one after another:
+ * left (h, hu, hv over the ny rows), right (the same), bottom (h, hu, hv
+ * over the nx columns), top (the same), each strip in increasing row or
+ * column order.  swe_part_edges writes all four edge strips of the current
+ * state; swe_part_set_ghosts reads the strips of the sides in the bitmask
+ * ``sides`` and leaves the rest of the buffer unread.  Stream-ordered; the
+ * buffer is the caller's.  With every rank's ghosts so exchanged, each
+ * step gives the single-grid result bit for bit.  SWE_EINVAL for walls or
+ * sides outside 0..15, a null buffer, or a context from swe_part_create
+ * with more than one partition.  swe_part_set_state / get_state / step /
+ * query / destroy apply as above (px = py = 1).
+ */
+swe_status swe_part_create_rank(int nx, int ny, int walls, double dx, double dy, double dt, double g,
+                                swe_part **out);
+swe_status swe_part_edges(swe_part *part, float *edges, void *stream);
+swe_status swe_part_set_ghosts(swe_part *part, const float *ghosts, int sides, void *stream);
+
 /* ==========================================================================
  * Region front end (Sec. 2.3 region functions; Sec. 3.1 statements; Sec.
  * 4.2.1 lowering).  The step and the wall fill written as array statements
@@ -422,8 +450,10 @@ swe_status swe_region_shapes(int nx, int ny, int *ext, int max_groups, int *n_gr
  * evaluation takes it (2; n even), or by CUDA's __fdiv_rn (1); which = 3
  * gives the reciprocal step of the statements' division alone, out[i] =
  * 1 / b[i] correctly rounded for 2^-20 <= b[i] < 2^20 whose significand is
- * not all ones (a is not read; other b give an undefined value).  Device
- * pointers, n >= 0; stream-ordered. */
+ * not all ones (a is not read; other b give an undefined value); which = 4
+ * gives the stencil kernels' approximate reciprocal of b[i] (rcp.approx,
+ * flushing subnormals; a is not read).  Device pointers, n >= 0;
+ * stream-ordered. */
 swe_status swe_selftest_div(const float *a, const float *b, float *out, int n, int which, void *stream);
 
 /* ==========================================================================

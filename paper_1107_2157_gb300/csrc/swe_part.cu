@@ -36,7 +36,8 @@ struct PartDev {
     long long pitch;  // >= nx + 8, a multiple of 32 floats
     long long plane;  // pitch * (ny + 2)
     int nx, ny;       // interior cells
-    int nbr[4];       // neighbouring partition on each side, -1 = global wall
+    int nbr[4];       // neighbouring partition on each side, -1 = global wall,
+                      // -2 = another rank's partition (ghosts written by the caller)
 };
 
 // Cell (i, j) of partition P in ghosted coordinates: i = 0 and i = nx + 1
@@ -72,6 +73,7 @@ __global__ void part_halo_kernel(const PartDev *__restrict__ parts, int n_parts,
         else if (side == SIDE_B) { gi = k + 1; gj = 0; }
         else { gi = k + 1; gj = P.ny + 1; }
         const int nb = P.nbr[side];
+        if (nb == -2) continue;  // filled by the caller from the neighbouring rank
         float h, u, v;
         if (nb >= 0) {
             const PartDev &Q = parts[nb];
@@ -93,6 +95,38 @@ __global__ void part_halo_kernel(const PartDev *__restrict__ parts, int n_parts,
         *cellp(P, b, 0, gi, gj) = h;
         *cellp(P, b, 1, gi, gj) = u;
         *cellp(P, b, 2, gi, gj) = v;
+    }
+}
+
+// Edge strips of a single partition (a rank's), packed side by side:
+// [left: h, hu, hv over ny rows][right: same][bottom: h, hu, hv over nx
+// columns][top: same].  Offsets of a side's strip in that layout:
+__host__ __device__ __forceinline__ long long strip_offset(int side, int nx, int ny)
+{
+    return side <= SIDE_R ? (long long)side * 3 * ny : 6LL * ny + (long long)(side - SIDE_B) * 3 * nx;
+}
+
+// edges[] <- the partition's interior cells along each side (to_ghosts =
+// false), or the ghost ring of the sides in ``sides`` <- ghosts[] (true).
+__global__ void part_strips_kernel(PartDev P, int b, float *__restrict__ strips, int sides, bool to_ghosts)
+{
+    const long long total = 6LL * P.ny + 6LL * P.nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int side = e < 6LL * P.ny ? (int)(e / (3LL * P.ny)) : SIDE_B + (int)((e - 6LL * P.ny) / (3LL * P.nx));
+        const int len = side <= SIDE_R ? P.ny : P.nx;
+        const long long r = e - strip_offset(side, P.nx, P.ny);
+        const int f = (int)(r / len), k = (int)(r % len);
+        int ei, ej, gi, gj;  // edge cell and ghost cell
+        if (side == SIDE_L) { ei = 1; gi = 0; ej = gj = k + 1; }
+        else if (side == SIDE_R) { ei = P.nx; gi = P.nx + 1; ej = gj = k + 1; }
+        else if (side == SIDE_B) { ej = 1; gj = 0; ei = gi = k + 1; }
+        else { ej = P.ny; gj = P.ny + 1; ei = gi = k + 1; }
+        if (to_ghosts) {
+            if (sides & (1 << side)) *cellp(P, b, f, gi, gj) = strips[e];
+        } else {
+            strips[e] = *cellp(P, b, f, ei, ej);
+        }
     }
 }
 
@@ -190,11 +224,7 @@ swe_status swe_part_create(int nx, int ny, int px, int py, double dx, double dy,
     p->ny = ny;
     p->px = px;
     p->py = py;
-    p->k.hx = (float)(0.5 * dt / dx);
-    p->k.hy = (float)(0.5 * dt / dy);
-    p->k.lx = (float)(dt / dx);
-    p->k.ly = (float)(dt / dy);
-    p->k.hg = (float)(0.5 * g);
+    p->k = make_coef<float>(dx, dy, dt, g);
     for (int a = 0; a <= px; ++a) p->xs.push_back((int)((long long)a * nx / px));
     for (int b = 0; b <= py; ++b) p->ys.push_back((int)((long long)b * ny / py));
     const int n = px * py;
@@ -318,6 +348,45 @@ swe_status swe_part_step(swe_part *p, int n_steps, void *stream)
         p->launches += 2;
     }
     return SWE_OK;
+}
+
+swe_status swe_part_create_rank(int nx, int ny, int walls, double dx, double dy, double dt, double g,
+                                swe_part **out)
+{
+    if (!out) return SWE_EINVAL;
+    *out = nullptr;
+    if (walls < 0 || walls > 15) return SWE_EINVAL;
+    swe_part *p = nullptr;
+    swe_status s = swe_part_create(nx, ny, 1, 1, dx, dy, dt, g, &p);
+    if (s != SWE_OK) return s;
+    PartDev &d = p->h_parts[0];
+    for (int side = 0; side < 4; ++side) d.nbr[side] = (walls & (1 << side)) ? -1 : -2;
+    if ((s = pst(cudaMemcpy(p->d_parts, p->h_parts.data(), sizeof(PartDev), cudaMemcpyHostToDevice))) != SWE_OK) {
+        swe_part_destroy(p);
+        return s;
+    }
+    *out = p;
+    return SWE_OK;
+}
+
+static swe_status part_strips(swe_part *p, float *strips, int sides, bool to_ghosts, cudaStream_t s)
+{
+    if (!p || !strips || p->px * p->py != 1 || sides < 0 || sides > 15) return SWE_EINVAL;
+    const PartDev &d = p->h_parts[0];
+    const long long total = 6LL * d.ny + 6LL * d.nx;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 1024);
+    part_strips_kernel<<<blocks, 256, 0, s>>>(d, p->cur, strips, sides, to_ghosts);
+    return pst(cudaGetLastError());
+}
+
+swe_status swe_part_edges(swe_part *p, float *edges, void *stream)
+{
+    return part_strips(p, edges, 15, false, static_cast<cudaStream_t>(stream));
+}
+
+swe_status swe_part_set_ghosts(swe_part *p, const float *ghosts, int sides, void *stream)
+{
+    return part_strips(p, const_cast<float *>(ghosts), sides, true, static_cast<cudaStream_t>(stream));
 }
 
 swe_status swe_part_query(swe_part *p, int key, long long *value)

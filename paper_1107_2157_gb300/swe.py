@@ -101,6 +101,9 @@ _SIGS = {
     "swe_part_get_state": (_i, [_vp, _vp, _vp, _vp, _ll, _vp]),
     "swe_part_step": (_i, [_vp, _i, _vp]),
     "swe_part_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
+    "swe_part_create_rank": (_i, [_i, _i, _i, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
+    "swe_part_edges": (_i, [_vp, _vp, _vp]),
+    "swe_part_set_ghosts": (_i, [_vp, _vp, _i, _vp]),
     "swe_region_create": (_i, [_i, _i, _i, _ll, _i, ctypes.POINTER(_vp)]),
     "swe_region_destroy": (None, [_vp]),
     "swe_region_step": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _d, _d, _d, _vp]),
@@ -338,6 +341,38 @@ class Partitioned:
               "swe_part_create")
         self.p = h.value
         self.nx, self.ny = nx, ny
+
+    @classmethod
+    def rank(cls, nx, ny, walls, dx, dy, dt, g):
+        """One rank's nx x ny partition; ``walls``: bitmask of its sides on
+        the grid boundary (1 left, 2 right, 4 bottom, 8 top)."""
+        self = cls.__new__(cls)
+        h = _vp()
+        check(lib().swe_part_create_rank(int(nx), int(ny), int(walls), dx, dy, dt, g, ctypes.byref(h)),
+              "swe_part_create_rank")
+        self.p = h.value
+        self.nx, self.ny = nx, ny
+        return self
+
+    def edges(self, out, stream=None):
+        """The four edge strips into the float32 CUDA tensor ``out`` of
+        6 (nx + ny) elements (layout in swe.h)."""
+        check(lib().swe_part_edges(self.p, self._strip_ptr(out), stream if stream is not None else current_stream()),
+              "swe_part_edges")
+
+    def set_ghosts(self, strips, sides, stream=None):
+        """The ghost strips of the sides in the bitmask ``sides`` from the
+        float32 CUDA tensor ``strips`` (same layout as ``edges``)."""
+        check(lib().swe_part_set_ghosts(self.p, self._strip_ptr(strips), int(sides),
+                                        stream if stream is not None else current_stream()), "swe_part_set_ghosts")
+
+    def _strip_ptr(self, t):
+        import torch
+        n = 6 * (self.nx + self.ny)
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError("expected a contiguous float32 CUDA tensor of %d elements" % n)
+        return t.data_ptr()
 
     def close(self):
         if getattr(self, "p", None):

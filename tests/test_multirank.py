@@ -59,9 +59,10 @@ def test_single_rank_needs_no_process_group():
 
 
 def _halo_rank(rank, world, port, px, py, nx, ny, steps, out):
-    """One partition per rank: exchange the halo over gloo, then one oracle
-    step (FP64) on the ghosted arrays, ``steps`` times; the interior goes
-    back to the parent."""
+    """One partition per rank: exchange the ghost strips that face other
+    ranks over gloo, fill the wall ghosts with the oracle's reflective rule,
+    then one oracle step (FP64) on the ghosted arrays, ``steps`` times; the
+    interior goes back to the parent."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -82,10 +83,12 @@ def _halo_rank(rank, world, port, px, py, nx, ny, steps, out):
             F = torch.zeros((y1 - y0 + 2, x1 - x0 + 2), dtype=torch.float64)
             F[1:-1, 1:-1] = torch.from_numpy(np.ascontiguousarray(full[y0:y1, x0:x1]))
             fields.append(F)
+        walls = P.wall_mask(rank, px, py)
         for _ in range(steps):
             P.exchange_halo(fields, rank, px, py)
-            (oH, oU, oV), _, _ = oracle.step_padded(*(np.ascontiguousarray(F.numpy()) for F in fields),
-                                                    1.0, 1.0, dt, 9.8)
+            arrs = [np.ascontiguousarray(F.numpy()) for F in fields]
+            oracle.fill_halo(*arrs, walls=walls)
+            (oH, oU, oV), _, _ = oracle.step_padded(*arrs, 1.0, 1.0, dt, 9.8)
             fields = [torch.from_numpy(x) for x in (oH, oU, oV)]
         out[rank] = [F[1:-1, 1:-1].numpy().copy() for F in fields]
     finally:
@@ -95,8 +98,10 @@ def _halo_rank(rank, world, port, px, py, nx, ny, steps, out):
 @pytest.mark.parametrize("px,py", [(2, 2), (3, 1), (1, 3)])
 def test_gloo_ranks_with_halo_exchange_equal_the_single_domain_bitwise(px, py):
     """Partitions on separate processes, ghost strips exchanged with
-    torch.distributed (gloo), each stepped by the FP64 oracle: the gathered
-    state equals the oracle on the whole grid bit for bit, walls included."""
+    torch.distributed (gloo) in the library's strip layout, each stepped by
+    the FP64 oracle: the gathered state equals the oracle on the whole grid
+    bit for bit, walls included.  (tests/test_gpu_multirank.py runs the same
+    exchange around the library's CUDA step.)"""
     import numpy as np
     sys.path.insert(0, ROOT)
     import oracle
@@ -137,3 +142,7 @@ def test_partition_layout_covers_the_grid_once():
     nb = P.neighbours(4, 3, 3)  # the centre of a 3 x 3 layout
     assert nb == {P.LEFT: 3, P.RIGHT: 5, P.BOTTOM: 1, P.TOP: 7}
     assert P.neighbours(0, 3, 3) == {P.LEFT: None, P.RIGHT: 1, P.BOTTOM: None, P.TOP: 3}
+    assert P.wall_mask(4, 3, 3) == 0 and P.wall_mask(0, 3, 3) == 1 | 4 and P.wall_mask(0, 1, 1) == 15
+    # strips tile the buffer of 6 (nx + ny) floats in the order left, right, bottom, top
+    sl = [P.strip_slice(s, 7, 5) for s in P.SIDES]
+    assert [(x.start, x.stop) for x in sl] == [(0, 15), (15, 30), (30, 51), (51, 72)]
