@@ -174,8 +174,11 @@ swe_status swe_query(swe_ctx *ctx, int key, long long *value);
  * Scratch: the partial sums live in a file-scope __device__ array of 1024
  * doubles (8 KB), which every GPU that loads the library holds until the
  * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, with the device current); make the first
- * call on each device before any stream capture.  All calls share the
+ * address (cudaGetSymbolAddress, with the device current) and keeps it for
+ * the life of the process; make the first call on each device before any
+ * stream capture.  A device reset (cudaDeviceReset, or anything else that
+ * destroys the device's primary context) invalidates that address: do not
+ * call swe_mass_noalloc on that device afterwards.  All calls share the
  * array and each call overwrites every partial it reads, so nothing needs
  * clearing, but calls that overlap on the GPU (other streams, other host
  * threads) race on it: serialise them.

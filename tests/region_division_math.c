@@ -15,10 +15,11 @@
  *      float y0 within the bound;
  *   2. the all-ones significand has a y0 within the bound for which it is
  *      not (why the division sends those divisors to the exact fallback);
- *   3. q = RN(a/b) for every significand b, a on both sides of several
- *      quotient midpoints and at random, y0 at both ends of the bound and in
- *      the middle.  The reference is the quotient in double rounded to float,
- *      which is correctly rounded (53 >= 2 * 24 + 2).
+ *   3. q = RN(a/b) for every 8th significand b and for all of the first and
+ *      last 4096 significands (about 1.06 million b), a on both sides of
+ *      several quotient midpoints and at random, y0 at both ends of the
+ *      bound and in the middle.  The reference is the quotient in double
+ *      rounded to float, which is correctly rounded (53 >= 2 * 24 + 2).
  * Prints one line "ok <counts>" or the first failures; exit status 0 = ok.
  */
 #include <math.h>
