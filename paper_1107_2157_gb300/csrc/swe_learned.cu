@@ -174,6 +174,7 @@ __device__ __forceinline__ void load16(const float *p, float (&b)[16])
 // Arms CPT accumulator columns at taddr with the bias (TMEM store); an odd
 // 8 columns first, so that every 16-column store starts on a multiple of 16
 // when taddr's column is a multiple of 16 or sits 8 past one.
+// The stores are issued back to back and waited for once.
 template <int CPT>
 __device__ __forceinline__ void arm(uint32_t taddr, const float *bias)
 {
@@ -182,28 +183,44 @@ __device__ __forceinline__ void arm(uint32_t taddr, const float *bias)
     if constexpr (LEAD == 8) {
         float b[16];
         load16(bias, b);  // 16 floats are readable: the bias block has 80
-        tc::st_x8(taddr, b);
+        tc::st_x8_async(taddr, b);
     }
 #pragma unroll
     for (int c = 0; c < CPT / 16; ++c) {
         float b[16];
         load16(bias + LEAD + 16 * c, b);
-        tc::st_x16(taddr + LEAD + 16 * c, b);
+        tc::st_x16_async(taddr + LEAD + 16 * c, b);
     }
+    tc::wait_st();
 }
 
-// CPT accumulator columns at taddr into v, in the same granules as arm.
+// CPT (8, 16 or 24) accumulator columns at taddr into v, in the same
+// granules as arm: the loads are issued back to back and waited for once.
 template <int CPT>
 __device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[CPT])
 {
-    constexpr int LEAD = CPT % 16;
-    if constexpr (LEAD == 8) tc::ld_x8(taddr, v);
+    static_assert(CPT == 8 || CPT == 16 || CPT == 24, "granules");
+    if constexpr (CPT == 8) {
+        uint32_t a[8];
+        tc::ld_x8_async(taddr, a);
+        tc::wait_ld(a);
 #pragma unroll
-    for (int c = 0; c < CPT / 16; ++c) {
-        float w[16];
-        tc::ld_x16(taddr + LEAD + 16 * c, w);
+        for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(a[i]);
+    } else if constexpr (CPT == 16) {
+        uint32_t b[16];
+        tc::ld_x16_async(taddr, b);
+        tc::wait_ld(b);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[LEAD + 16 * c + i] = w[i];
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(b[i]);
+    } else {
+        uint32_t a[8], b[16];
+        tc::ld_x8_async(taddr, a);
+        tc::ld_x16_async(taddr + 8, b);
+        tc::wait_ld(a, b);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(a[i]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[8 + i] = __uint_as_float(b[i]);
     }
 }
 
@@ -535,7 +552,7 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                     if (lw_thread && r3 >= 0 && r3 < H) {
                         const uint32_t ta = t3 + mod3(r3) * 16;
                         float v[16];
-                        tc::ld_x16(ta, v);
+                        tmem_load<16>(ta, v);
                         arm<16>(ta, sBias + 64);
                         if (inside) {
                             const int s3 = lws >= 6 ? lws - 6 : lws + 1;  // (t - 6) mod 7
