@@ -102,11 +102,30 @@ def test_more_entry_points_reject_bad_arguments_before_device_work(libswe):
 
     sd = libswe.swe_selftest_div
     sd.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]
-    assert sd(fake, fake, fake, 16, 4, None) == EINVAL      # no such mode
+    assert sd(fake, fake, fake, 16, 5, None) == EINVAL      # no such mode
     assert sd(fake, fake, fake, 15, 2, None) == EINVAL      # pairs need an even count
     assert sd(fake, fake, fake, -1, 0, None) == EINVAL
     assert sd(None, fake, fake, 16, 0, None) == EINVAL
     assert sd(fake, fake, fake, 0, 3, None) == 0            # nothing to do
+
+    pr = libswe.swe_probe_rate
+    pr.argtypes = [c_int, ctypes.POINTER(c_double)]
+    rate = c_double(0.0)
+    assert pr(3, ctypes.byref(rate)) == EINVAL              # no such kind
+    assert pr(0, None) == EINVAL
+
+    rk = libswe.swe_part_create_rank
+    rk.argtypes = [c_int, c_int, c_int] + [c_double] * 4 + [ctypes.POINTER(c_void_p)]
+    assert rk(64, 64, 16, 1.0, 1.0, 0.1, 9.8, ctypes.byref(out)) == EINVAL  # walls outside 0..15
+    assert rk(64, 64, -1, 1.0, 1.0, 0.1, 9.8, ctypes.byref(out)) == EINVAL
+    assert rk(64, 64, 15, 1.0, 1.0, 0.1, 9.8, None) == EINVAL
+    assert out.value is None
+    pe = libswe.swe_part_edges
+    pe.argtypes = [c_void_p, c_void_p, c_void_p]
+    assert pe(None, fake, None) == EINVAL
+    pg = libswe.swe_part_set_ghosts
+    pg.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
+    assert pg(None, fake, 15, None) == EINVAL
 
     sw = libswe.swe_selftest_wait
     sw.argtypes = [c_int, c_double, c_void_p]

@@ -441,3 +441,78 @@ def test_every_two_step_shape_equals_the_one_step_kernel_bitwise(variant):
         assert grid.check() == 0
     for k in range(3):
         assert np.array_equal(got[k], ref[k]), (variant, k)
+
+
+def test_fp32_mass_is_the_exact_sum_on_awkward_data():
+    """The FP32 mass sums the depths exactly in 64-bit integers (flushing to
+    FP64 only when the largest exponent rises): on depths within a few
+    binades, straddling powers of two, with zeros, negative values and row
+    tails (nx % 4 != 0), it equals the exactly rounded sum of the same values
+    (math.fsum) to a few units in the last place; over 50 binades, where the
+    values far below a thread's largest go to its FP64 total, to 1e-14."""
+    import math
+    from paper_1107_2157_gb300 import Grid
+    rng = np.random.default_rng(23)
+    nx, ny = 1027, 333
+    cases = {
+        "one binade": 1.0 + 0.99 * rng.random((ny, nx)),
+        "straddling 1 and 2": 0.7 + 1.6 * rng.random((ny, nx)),
+        "wide": 2.0 ** rng.uniform(-30, 20, (ny, nx)),
+        "signs and zeros": np.where(rng.random((ny, nx)) < 0.3, 0.0, rng.standard_normal((ny, nx))),
+    }
+    for name, h in cases.items():
+        h = h.astype(np.float32)
+        z = np.zeros_like(h)
+        with Grid(nx, ny, 1.0, 1.0, 0.01, G, dtype="f32") as grid:
+            grid.set_state(h, z, z)
+            m = grid.mass()
+        want = math.fsum(h.astype(np.float64).ravel())
+        tol = 1e-14 * abs(want) if name == "wide" else 4 * math.ulp(abs(want))
+        assert abs(m - want) <= tol, (name, m, want)
+
+
+def test_rank_partition_edges_and_ghosts_follow_the_strip_layout():
+    """swe_part_edges writes left, right, bottom, top edge strips (h, hu, hv
+    each, in row / column order); swe_part_set_ghosts writes only the sides
+    in its mask, and a step then reads them: a partition whose every side
+    faces another rank, fed the ghosts a wall would give, steps exactly like
+    a partition with four walls."""
+    import torch
+    from paper_1107_2157_gb300 import Partitioned
+    from paper_1107_2157_gb300 import partition as P
+    nx, ny = 37, 23
+    s = si.smooth_flow_state(9, nx, ny).rounded_to(np.float32)
+    fields = [np.ascontiguousarray(a, np.float32) for a in (s.h, s.hu, s.hv)]
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.3)
+    n = 6 * (nx + ny)
+    open_p = Partitioned.rank(nx, ny, 0, 1.0, 1.0, dt, G)
+    walls_p = Partitioned.rank(nx, ny, 15, 1.0, 1.0, dt, G)
+    try:
+        for p in (open_p, walls_p):
+            p.set_state(*fields)
+        edges = torch.empty(n, dtype=torch.float32, device="cuda")
+        open_p.edges(edges)
+        e = edges.cpu().numpy()
+        want = {P.LEFT: [f[:, 0] for f in fields], P.RIGHT: [f[:, -1] for f in fields],
+                P.BOTTOM: [f[0, :] for f in fields], P.TOP: [f[-1, :] for f in fields]}
+        for side in P.SIDES:
+            got = e[P.strip_slice(side, nx, ny)].reshape(3, -1)
+            for k in range(3):
+                assert np.array_equal(got[k], want[side][k]), (side, k)
+        # the reflective ghosts of every side: edge cells, normal momentum negated
+        ghosts = np.empty(n, np.float32)
+        for side in P.SIDES:
+            strip = np.stack(want[side]).copy()
+            strip[1 if side in (P.LEFT, P.RIGHT) else 2] *= -1.0
+            ghosts[P.strip_slice(side, nx, ny)] = strip.ravel()
+        g = torch.from_numpy(ghosts).cuda()
+        open_p.set_ghosts(g, 1 | 2)       # left and right now
+        open_p.set_ghosts(g, 4 | 8)       # then bottom and top
+        open_p.step(1)
+        walls_p.step(1)
+        a, b = open_p.get_state(), walls_p.get_state()
+        for k in range(3):
+            assert np.array_equal(a[k], b[k]), k
+    finally:
+        open_p.close()
+        walls_p.close()
