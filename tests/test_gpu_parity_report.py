@@ -34,17 +34,25 @@ def _record(key, value):
             json.dump(REPORT, f, indent=1)
 
 
-def _f32_entry(worst, strict, worst_b32):
+def _f32_entry(worst, strict, worst_b32, diff):
     ok = all(worst[k] <= max(TOL_F32, B32_RATIO * worst_b32[k]) for k in range(3))
     return {"gpu": worst, "gpu_strict": strict, "binary32_oracle": worst_b32,
+            "gpu_minus_binary32": diff,
             "passes_2e-5": max(worst) <= TOL_F32, "binary32_passes_2e-5": max(worst_b32) <= TOL_F32,
             "within_bar": ok}
+
+
+def _diff(got, b32, ref, acc):
+    """max|gpu - binary32 oracle| per field, on the parity scales of ref."""
+    from parity import scales
+    den = scales(ref)
+    return [max(acc[k], float(np.abs(np.asarray(got[k], np.float64) - b32[k]).max()) / den[k]) for k in range(3)]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_report_128_grid_all_seeds(dtype):
     npd = np.float64 if dtype == "f64" else np.float32
-    worst, strict, worst_b32 = [0.0] * 3, [0.0] * 3, [0.0] * 3
+    worst, strict, worst_b32, diff = [0.0] * 3, [0.0] * 3, [0.0] * 3, [0.0] * 3
     for seed in range(10):
         s = si.single_bump_state(seed).rounded_to(npd)
         dt = oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.2)
@@ -55,11 +63,12 @@ def test_report_128_grid_all_seeds(dtype):
         if dtype == "f32":
             b32 = oracle.run_f32(s.h, s.hu, s.hv, 1.0, 1.0, dt, G, 100)
             worst_b32 = [max(a, b) for a, b in zip(worst_b32, rel_errors(b32, ref))]
+            diff = _diff(got, b32, ref, diff)
     if dtype == "f64":
         _record("128x128_100steps_f64", {"gpu": worst, "gpu_strict": strict})
         assert max(worst) <= TOL_F64
     else:
-        e = _f32_entry(worst, strict, worst_b32)
+        e = _f32_entry(worst, strict, worst_b32, diff)
         _record("128x128_100steps_f32", e)
         assert e["within_bar"], e
 
@@ -74,7 +83,7 @@ def test_report_ensemble_instances_500_steps():
     states = [si.ensemble_state(2, i, *sizes_all[i]).rounded_to(np.float32) for i in pick]
     dts = [oracle.cfl_dt(s.h, s.hu, s.hv, 1.0, 1.0, G, 0.2) for s in states]
     oracle.set_threads(os.cpu_count() or 1)
-    worst, strict, worst_b32 = [0.0] * 3, [0.0] * 3, [0.0] * 3
+    worst, strict, worst_b32, diff = [0.0] * 3, [0.0] * 3, [0.0] * 3, [0.0] * 3
     try:
         with Batch(sizes, 1.0, 1.0, dts, G) as b:
             for i, s in enumerate(states):
@@ -87,9 +96,10 @@ def test_report_ensemble_instances_500_steps():
                 worst = [max(a, c) for a, c in zip(worst, rel_errors(got, ref))]
                 strict = [max(a, c) for a, c in zip(strict, strict_errors(got, ref))]
                 worst_b32 = [max(a, c) for a, c in zip(worst_b32, rel_errors(b32, ref))]
+                diff = _diff(got, b32, ref, diff)
     finally:
         oracle.set_threads(1)
-    e = _f32_entry(worst, strict, worst_b32)
+    e = _f32_entry(worst, strict, worst_b32, diff)
     _record("ensemble_8_instances_500steps_f32", e)
     assert e["within_bar"], e
 
@@ -117,7 +127,7 @@ def test_report_8192_grid_windows(dtype):
         h = si.large_grid_state(seed=1, n=n, window=w).h.astype(npd).astype(np.float64)
         return h, np.zeros_like(h), np.zeros_like(h)
 
-    worst, worst_b32 = [0.0] * 3, [0.0] * 3
+    worst, worst_b32, diff = [0.0] * 3, [0.0] * 3, [0.0] * 3
     for w in _full_windows(n):
         ref = oracle.run_window(ic, n, n, w, 1.0, 1.0, dt, G, steps)
         b32 = oracle.run_window(ic, n, n, w, 1.0, 1.0, dt, G, steps, binary32=True) if dtype == "f32" else None
@@ -127,10 +137,11 @@ def test_report_8192_grid_windows(dtype):
             worst[k] = max(worst[k], float(np.abs(sub - ref[k]).max() / den[k]))
             if b32 is not None:
                 worst_b32[k] = max(worst_b32[k], float(np.abs(b32[k].astype(np.float64) - ref[k]).max() / den[k]))
+                diff[k] = max(diff[k], float(np.abs(sub - b32[k]).max() / den[k]))
     if dtype == "f64":
         _record("8192x8192_100steps_f64_windows", {"gpu": worst})
         assert max(worst) <= TOL_F64
     else:
-        e = _f32_entry(worst, worst, worst_b32)
+        e = _f32_entry(worst, worst, worst_b32, diff)
         _record("8192x8192_100steps_f32_windows", e)
         assert e["within_bar"], e
