@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_GRID, help="grid size (default 8192)")
     p.add_argument("--kernel", type=int, default=0, help="swe_kernel (0 = auto)")
-    p.add_argument("--variant", type=int, default=None, help="two-step kernel shape 0..4 (with --kernel 3; 4 = persistent 8x4)")
+    p.add_argument("--variant", type=int, default=None, help="two-step kernel shape 0..8 (with --kernel 3; 4 = persistent 8x4 tiles, 5..8 = streaming warps; default 5 for FP32)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="grid: leave out the ensemble and FP64 sub-records of the default line")
@@ -130,6 +130,8 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "lw_tb2_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_temporal.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
                              "paper_1107_2157_gb300/csrc/swe_device.cuh"),
+    "lw_stream_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_stream.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
+                                "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "region_lw_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_region.cu", "paper_1107_2157_gb300/csrc/swe_region.cuh",
                                 "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "region_lw_kernel<float, bed>": ("paper_1107_2157_gb300/csrc/swe_region.cu",
@@ -143,6 +145,7 @@ KERNEL_SOURCES = {
 # swe_kernel value -> (kernel name, algorithmic bytes per cell-update of its state layout)
 STEP_KERNELS = {1: ("lw_naive_kernel<float>", 24), 2: ("lw_tiled_kernel<float>", 24),
                 3: ("lw_tb2_kernel<float>", 24), 4: ("lw_packed_kernel", 32)}
+STREAM_SHAPES = (5, 6, 7, 8)  # two-step shapes run by lw_stream_kernel
 
 
 def kernel_source_hash(kernel_name="lw_tiled_kernel<float>"):
@@ -374,6 +377,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = grid.query(swe.SWE_Q_LAUNCHES) - launches0
     kname, bytes_per_update = STEP_KERNELS[int(grid.query(swe.SWE_Q_KERNEL))]
+    if int(grid.query(swe.SWE_Q_SHAPE)) in STREAM_SHAPES:
+        kname = "lw_stream_kernel<float>"
     steps_per_launch = int(grid.query(swe.SWE_Q_STEPS_PER_LAUNCH))
     t_job = e0.elapsed_time(e3) / 1e3
     t_steps = e1.elapsed_time(e2) / 1e3

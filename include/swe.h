@@ -70,9 +70,14 @@ typedef struct {
     int dtype;   /* swe_dtype; default SWE_F32 */
     int kernel;  /* swe_kernel; default SWE_KERNEL_AUTO */
     int depth;   /* 0 = default; SWE_KERNEL_TEMPORAL runs 2 steps per launch */
-    int reserved[5]; /* reserved[0]: two-step kernel shape + 1 (0 = the default, shape 4); shapes 0..3 take
-                        one CTA per tile (warps x rows: 4x8, 8x4, 4x4, 8x2), shape 4 is 8x4 with persistent
-                        CTAs that prefetch their next tile; others 0 */
+    int reserved[5]; /* reserved[0]: two-step kernel shape + 1 (0 = the default: shape 5 for FP32, 4 for
+                        FP64).  Shapes 0..3 take one CTA per tile (warps x rows: 4x8, 8x4, 4x4, 8x2),
+                        shape 4 is 8x4 with persistent CTAs that prefetch their next tile.  Shapes 5..8
+                        (FP32 only, SWE_EUNSUPPORTED for FP64) are warps that stream up column strips
+                        with the intermediate rows in registers and x-neighbours from warp shuffles
+                        (5: 120-column strips, two 4-row TMA chunks per warp; 6: three chunks; 7:
+                        56-column strips; 8: four 2-row chunks).  All shapes give the same bits.
+                        Others 0 */
 } swe_options;
 
 /* Fills *opt with the defaults (FP32, automatic kernel choice). */
@@ -149,7 +154,8 @@ typedef enum {
     SWE_Q_TILE_X = 4,           /* tile width in cells */
     SWE_Q_TILE_Y = 5,           /* tile height in cells */
     SWE_Q_STATE_PTR = 6,        /* device address of the current H plane (SWE_KERNEL_PACKED: of the packed state) */
-    SWE_Q_STEPS_PER_LAUNCH = 7  /* steps a full step-kernel launch advances */
+    SWE_Q_STEPS_PER_LAUNCH = 7, /* steps a full step-kernel launch advances */
+    SWE_Q_SHAPE = 8             /* two-step kernel shape (see swe_options), -1 for the other kernels */
 } swe_query_key;
 
 /* Writes the value of ``key`` to *value. */

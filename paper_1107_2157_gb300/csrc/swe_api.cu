@@ -183,6 +183,8 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     if (o.kernel < SWE_KERNEL_AUTO || o.kernel > SWE_KERNEL_PACKED) return SWE_EINVAL;
     if (o.kernel == SWE_KERNEL_PACKED && o.dtype != SWE_F32) return SWE_EUNSUPPORTED;
     if (o.depth < 0 || o.depth > 2) return SWE_EUNSUPPORTED;
+    if (o.reserved[0] >= 6 && o.reserved[0] <= 9 && o.dtype != SWE_F32)
+        return SWE_EUNSUPPORTED;  // the streaming shapes are FP32
 
     swe_ctx *c = new (std::nothrow) swe_ctx();
     if (!c) return SWE_ENOMEM;
@@ -203,7 +205,8 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     // gain nothing at GB300's FP64 rate).
     c->kernel = o.kernel != SWE_KERNEL_AUTO ? o.kernel : (o.dtype == SWE_F32 ? SWE_KERNEL_TEMPORAL : SWE_KERNEL_TILED);
     c->depth = c->kernel == SWE_KERNEL_TEMPORAL ? 2 : 1;
-    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 5) ? o.reserved[0] - 1 : 4;
+    // two-step shape: 5 (streaming warps) for FP32, 4 (persistent tiles) for FP64
+    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 9) ? o.reserved[0] - 1 : (o.dtype == SWE_F32 ? 5 : 4);
 
     const size_t bytes = 3 * c->plane * c->esize;
     swe_status st = SWE_OK;
@@ -403,6 +406,7 @@ swe_status swe_query(swe_ctx *c, int key, long long *value)
         case SWE_Q_LAUNCHES: *value = c->launches; break;
         case SWE_Q_TILE_X: *value = c->kernel == SWE_KERNEL_NAIVE ? 64 : tiled_geom(c->dtype).tile_x; break;
         case SWE_Q_STEPS_PER_LAUNCH: *value = c->depth; break;
+        case SWE_Q_SHAPE: *value = c->kernel == SWE_KERNEL_TEMPORAL ? c->tb_variant : -1; break;
         case SWE_Q_TILE_Y: *value = c->kernel == SWE_KERNEL_NAIVE ? 4 : tiled_geom(c->dtype).tile_y; break;
         case SWE_Q_STATE_PTR:
             // packed contexts: the packed state (h, hu, hv, 0 per cell)

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(NWARP * 32) lw_tb2_kernel(const __grid_constan
 // ~112 KB smem), 1: 8x4 (128x32, 256 threads), 2: 4x4 (128x16, ~61 KB),
 // 3: 8x2 (128x16, 256 threads), all with one CTA per tile; 4: 8x4 with
 // persistent CTAs (as many as fit on the device, each prefetching its next
-// tile under phase 2).
+// tile under phase 2).  5..8 (FP32 only): warps streaming up column strips
+// (swe_stream.cu).
 template <typename T, int W, int R>
 struct TbShape {
     using Cfg = Tb2Cfg<T, W, R>;
@@ -88,9 +89,14 @@ static void tb2_box_t(int *bw, int *bh)
     *bh = S::Cfg::BH_IN;
 }
 
+bool stream_box(int variant, int *bw, int *bh);
+cudaError_t launch_stream(int variant, const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
+                          long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+
 void tb2_box(int dtype, int variant, int *bw, int *bh)
 {
     const bool d = dtype == SWE_F64;
+    if (!d && stream_box(variant, bw, bh)) return;
     switch (variant) {
         case 1:
         case 4: d ? tb2_box_t<double, TbShape<double, 8, 4>>(bw, bh) : tb2_box_t<float, TbShape<float, 8, 4>>(bw, bh); break;
@@ -149,6 +155,7 @@ cudaError_t launch_tb2(int dtype, int variant, const CUtensorMap *maps_in, void 
 {
     if (dtype == SWE_F64)
         return launch_tb2_v<double>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
+    if (variant >= 5) return launch_stream(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
     return launch_tb2_v<float>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
 }
 

@@ -26,7 +26,7 @@ SWE_FLAG_NONPOSITIVE, SWE_FLAG_MASS, SWE_FLAG_TIMEOUT, SWE_FLAG_FALLBACK = 1, 2,
  SWE_BQ_STAGES, SWE_BQ_DEPTH, SWE_BQ_GRAPH, SWE_BQ_LAUNCHES, SWE_BQ_TUNED, SWE_BQ_CELLS,
  SWE_BQ_VARIANT_COUNT) = range(13)
 (SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
- SWE_Q_STATE_PTR, SWE_Q_STEPS_PER_LAUNCH) = range(8)
+ SWE_Q_STATE_PTR, SWE_Q_STEPS_PER_LAUNCH, SWE_Q_SHAPE) = range(9)
 SWE_PQ_PARTS, SWE_PQ_HALO_CELLS, SWE_PQ_LAUNCHES, SWE_PQ_ERROR = range(4)
 SWE_RQ_LAUNCHES, SWE_RQ_TILE_X, SWE_RQ_TILE_Y, SWE_RQ_SMEM, SWE_RQ_ERROR = range(5)
 

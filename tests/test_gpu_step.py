@@ -426,7 +426,7 @@ def test_stencil_reciprocal_halves_when_its_argument_doubles():
 @pytest.mark.parametrize("variant,nx,ny", [(0, 1411, 777), (1, 1411, 777), (2, 1411, 777), (3, 1411, 777),
                                            (4, 1411, 777), (4, 130, 12811), (4, 257, 3001)])
 def test_every_two_step_shape_equals_the_one_step_kernel_bitwise(variant, nx, ny):
-    """Shapes 0..3 take one CTA per tile, shape 4 (the FP32 default) runs
+    """Shapes 0..3 take one CTA per tile, shape 4 (the FP64 default) runs
     persistent CTAs that prefetch their next tile: all give the one-step
     kernel's bits, with ragged edges and an odd step count.  The tall grids
     have more tiles than resident CTAs, so each persistent CTA takes
@@ -443,6 +443,55 @@ def test_every_two_step_shape_equals_the_one_step_kernel_bitwise(variant, nx, ny
         assert grid.check() == 0
     for k in range(3):
         assert np.array_equal(got[k], ref[k]), (variant, k)
+
+
+# widths around the strip ends of the streaming shapes (56 and 120 columns)
+STREAM_WIDTHS = sorted({w for k in (1, 2, 3) for out in (56, 120) for w in
+                        (k * out - 2, k * out - 1, k * out, k * out + 1, k * out + 2, k * out + 3)})
+STREAM_CASES = [(v, nx, ny) for v in (5, 6, 7, 8) for nx, ny in ((1411, 777), (130, 12811), (257, 3001))] + \
+    [(v, nx, ny) for v in (5, 7) for nx, ny in [(1, 1), (2, 3), (5, 2), (8, 4099)] +
+     [(w, 3 + w % 37) for w in STREAM_WIDTHS]]
+
+
+@pytest.mark.parametrize("variant,nx,ny", STREAM_CASES)
+def test_streaming_two_step_shapes_equal_the_one_step_kernel_bitwise(variant, nx, ny):
+    """Shapes 5..8 stream warps up column strips (56 stored columns per warp
+    for one cell pair per lane, 120 for two) with the intermediate rows in
+    registers and the walls as mirrored ghost columns.  The widths put the
+    right wall in every lane position around a strip's end (including the
+    width at which a strip's last stored column reads the ghost column), one-
+    and two-row grids start and end a run on both walls at once, and the tall
+    grids cut each strip into many row ranges: all give the one-step
+    kernel's bits."""
+    from paper_1107_2157_gb300 import Grid
+    steps = 7
+    s = si.smooth_flow_state(4321 + nx, nx, ny).rounded_to(np.float32)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 0.9, 1.1, G, 0.3)
+    ref = run_gpu(s, 0.9, 1.1, dt, G, steps, "f32", KERNELS["tiled"])
+    with Grid(nx, ny, 0.9, 1.1, dt, G, dtype="f32", kernel=3, variant=variant) as grid:
+        grid.set_state(*(np.ascontiguousarray(a, np.float32) for a in (s.h, s.hu, s.hv)))
+        grid.step(steps)
+        got = grid.get_state()
+        assert grid.check() == 0
+    for k in range(3):
+        bad = np.argwhere(got[k] != ref[k])
+        assert bad.size == 0, (variant, k, bad[:4], got[k][tuple(bad[0])], ref[k][tuple(bad[0])])
+
+
+def test_two_step_defaults_and_fp32_only_shapes():
+    """The FP32 two-step default is streaming shape 5, the FP64 one tile
+    shape 4; the streaming shapes refuse FP64."""
+    from paper_1107_2157_gb300 import Grid, SweError, swe
+    with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f32", kernel=3) as grid:
+        assert grid.query(swe.SWE_Q_SHAPE) == 5
+    with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f64", kernel=3) as grid:
+        assert grid.query(swe.SWE_Q_SHAPE) == 4
+    with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f32", kernel=2) as grid:
+        assert grid.query(swe.SWE_Q_SHAPE) == -1
+    for v in (5, 6, 7, 8):
+        with pytest.raises(SweError) as e:
+            Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f64", kernel=3, variant=v)
+        assert e.value.status == 6  # SWE_EUNSUPPORTED
 
 
 def test_fp32_mass_is_the_exact_sum_on_awkward_data():
