@@ -382,22 +382,41 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
     return ok;
 }
 
-// The grid's NS strips are cut into K row ranges; warp gw takes strip
-// gw % NS of row range gw / NS (warps beyond K NS take nothing).  Warps that
-// run at the same time then cover all strips of the same rows, so DRAM sees
-// whole grid rows and a strip's overlap columns are read from L2.
+// The grid's NS strips are cut into K row ranges; warp gw < K NS takes strip
+// gw % NS of row range gw / NS.  Warps that run at the same time then cover
+// all strips of the same rows, so DRAM sees whole grid rows and a strip's
+// overlap columns are read from L2.  The first and the last strip hold the
+// walls, and their rows cost more (ghost columns); they are cut into Ke > K
+// ranges instead, the ranges K .. Ke - 1 going to the warps after K NS, so
+// that their warps end with the others.
 template <int VP, int LO, int NO, int CR, int NSLOT, int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     lw_stream_kernel(const __grid_constant__ CUtensorMap mH, const __grid_constant__ CUtensorMap mU,
                      const __grid_constant__ CUtensorMap mV, float *__restrict__ oH, float *__restrict__ oU,
-                     float *__restrict__ oV, int nx, int ny, long long pitch, int K, Coef<float> k, int *err)
+                     float *__restrict__ oV, int nx, int ny, long long pitch, int K, int Ke, Coef<float> k,
+                     int *err)
 {
     using C = StreamCfg<VP, LO, NO, CR, NSLOT, WARPS>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ns = (nx + C::OUT - 1) / C::OUT;
+    const int ne = ns == 1 ? 1 : 2;  // strips 0 and ns - 1
     const int gw = blockIdx.x * WARPS + warp;
-    if (gw >= K * ns) return;
+    int s, j, R;  // strip, row range, ranges of the strip
+    if (gw < K * ns) {
+        s = gw % ns;
+        j = gw / ns;
+        R = (s == 0 || s == ns - 1) ? Ke : K;
+    } else if (gw < K * ns + ne * (Ke - K)) {
+        const int e = (gw - K * ns) / (Ke - K);
+        s = e == 0 ? 0 : ns - 1;
+        j = K + (gw - K * ns) % (Ke - K);
+        R = Ke;
+    } else {
+        return;
+    }
+    const int ya = (int)((long long)j * ny / R), yb = (int)((long long)(j + 1) * ny / R);
+    if (ya >= yb) return;
     StreamWarp<VP, LO, NO, CR, NSLOT, WARPS> w;
     w.mH = &mH;
     w.mU = &mU;
@@ -407,14 +426,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     w.phase = 0;
     w.err = err;
     if (lane == 0) {
-        for (int j = 0; j < NSLOT; ++j) mbar_init(w.bars + j, 1);
+        for (int i = 0; i < NSLOT; ++i) mbar_init(w.bars + i, 1);
         fence_mbar_init();
     }
     __syncwarp();
     const Coef2 k2 = coef2(k);
-    const int s = gw % ns, j = gw / ns;
-    const int ya = (int)((long long)j * ny / K), yb = (int)((long long)(j + 1) * ny / K);
-    if (ya >= yb) return;
     const int xs = s * C::OUT;
     // the stored columns read input columns xs - 2 .. xs + OUT + 1: a strip
     // whose range reaches column -1 or nx fills that ghost column (held by
@@ -428,28 +444,32 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 
 // Launch shapes (two-step variants 5..8): pairs per lane, first stored
 // lane, stored lanes, rows per TMA chunk, chunks per warp, warps per CTA,
-// CTAs per SM the registers are capped for.  Measured on GB300 at 8192^2
-// (ms per two-step launch): 5: 0.327, 6: 0.328, 7: 0.371, 8: 0.342; a
-// 128-register cap for two pairs per lane spills 1.1 KB a thread.  The grid holds K strips' worth of warps, K as large as the
-// resident warps allow with at least kMinRows rows per range.
+// CTAs per SM the registers are capped for, and the wall strips' row ranges
+// per interior strip's, in eighths.  Measured on GB300 at 8192^2 (ms per
+// two-step launch, equal ranges for all strips): 5: 0.327, 6: 0.328, 7:
+// 0.371, 8: 0.342; a 128-register cap for two pairs per lane spills 1.1 KB a
+// thread.  The wall strips' warps are the last to finish with equal ranges:
+// 1.125, 1.25 and 1.5 times as many ranges give shape 5 0.308, 0.307 and
+// 0.305 ms; beyond 1.5 the resident warps no longer hold 26 ranges of every
+// interior strip, and 25 give 0.316.
 constexpr int kMinRows = 16;
 template <int VARIANT>
 struct StreamShape;
 template <>
 struct StreamShape<5> {  // the FP32 default: 120-column strips, two pairs per lane, two 4-row chunks
-    static constexpr int VP = 2, LO = 1, NO = 30, CR = 4, SLOTS = 2, WARPS = 4, MINB = 3;
+    static constexpr int VP = 2, LO = 1, NO = 30, CR = 4, SLOTS = 2, WARPS = 4, MINB = 3, EW8 = 12;
 };
 template <>
 struct StreamShape<6> {  // as 5 with three chunks per warp
-    static constexpr int VP = 2, LO = 1, NO = 30, CR = 4, SLOTS = 3, WARPS = 4, MINB = 3;
+    static constexpr int VP = 2, LO = 1, NO = 30, CR = 4, SLOTS = 3, WARPS = 4, MINB = 3, EW8 = 12;
 };
 template <>
 struct StreamShape<7> {  // 56-column strips (lanes 2..29), one pair per lane: 16 warps per SM
-    static constexpr int VP = 1, LO = 2, NO = 28, CR = 4, SLOTS = 3, WARPS = 4, MINB = 4;
+    static constexpr int VP = 1, LO = 2, NO = 28, CR = 4, SLOTS = 3, WARPS = 4, MINB = 4, EW8 = 12;
 };
 template <>
 struct StreamShape<8> {  // as 5 with four 2-row chunks
-    static constexpr int VP = 2, LO = 1, NO = 30, CR = 2, SLOTS = 4, WARPS = 4, MINB = 3;
+    static constexpr int VP = 2, LO = 1, NO = 30, CR = 2, SLOTS = 4, WARPS = 4, MINB = 3, EW8 = 12;
 };
 
 template <int V>
@@ -494,14 +514,19 @@ static cudaError_t launch_stream_t(const CUtensorMap *maps, void *out, size_t pl
         ctas = sms * std::max(per_sm, 1);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    // K row ranges of at least kMinRows rows, K strips' worth of warps at most
-    // the resident ones
+    // K row ranges of at least kMinRows rows, the wall strips Ke = K EW8 / 8
+    // (rounded up); K as large as the resident warps allow
     const int ns = (nx + C::OUT - 1) / C::OUT;
-    const int K = std::max(1, std::min(ctas * S::WARPS / ns, (ny + kMinRows - 1) / kMinRows));
-    const int grid = (K * ns + S::WARPS - 1) / S::WARPS;
+    const int ne = ns == 1 ? 1 : 2;
+    const int slots = ctas * S::WARPS;
+    int K = std::max(1, std::min(slots / ns, (ny + kMinRows - 1) / kMinRows));
+    auto walls = [&](int k) { return std::max(k, (k * S::EW8 + 7) / 8); };
+    while (K > 1 && K * ns + ne * (walls(K) - K) > slots) --K;
+    const int Ke = walls(K);
+    const int grid = (K * ns + ne * (Ke - K) + S::WARPS - 1) / S::WARPS;
     float *b = static_cast<float *>(out);
     kern<<<grid, S::WARPS * 32, C::SMEM, s>>>(maps[0], maps[1], maps[2], b, b + plane, b + 2 * plane, nx, ny,
-                                                   pitch, K, make_coef<float>(dx, dy, dt, g), err);
+                                                   pitch, K, Ke, make_coef<float>(dx, dy, dt, g), err);
     return cudaGetLastError();
 }
 
