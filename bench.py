@@ -91,7 +91,7 @@ def workload_config(n, steps):
                     "sigma U[8,64] cells, seed 1), hu = hv = 0, reflective walls, dx = dy = 1, g = 9.8, "
                     "dt = FP64 CFL 0.2 at t = 0, two-step Lax-Wendroff" % (n, n),
         "nx": n, "ny": n, "steps_timed": steps,
-        "job": "FP64 CFL dt + K steps + FP64 mass check",
+        "job": "FP64 CFL dt + K steps + FP64 mass check in one swe_run call (dt stays on the device)",
         "l2": "no flush: the state (3 x %d MB per buffer) is larger than L2 (129 MB)" % (n * n * 4 // 2**20),
         "parallelism": "replicas (one independent grid per GPU)",
     }
@@ -347,10 +347,7 @@ def run_ours(args):
 
     # --- warm-up -------------------------------------------------------------------------
     grid.set_state(h_dev, z_dev, z_dev, stream=sp)
-    dt = grid.cfl_dt(CFL, stream=sp)
-    grid.set_dt(dt)
-    grid.step(args.warmup, stream=sp)
-    grid.mass(stream=sp)
+    grid.run(args.warmup, CFL, stream=sp)
 
     sampler = ClockSampler(dev) if rank == 0 else None
     if sampler:
@@ -364,14 +361,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
     launches0 = grid.query(swe.SWE_Q_LAUNCHES)
-    e0.record(stream)
-    dt = grid.cfl_dt(CFL, stream=sp)
-    grid.set_dt(dt)
-    e1.record(stream)
-    grid.step(args.steps, stream=sp)
-    e2.record(stream)
-    mass = grid.mass(stream=sp)
-    e3.record(stream)
+    # one job: the FP64 CFL dt, K steps with it and the FP64 mass (swe_run: dt
+    # stays on the device, one host synchronisation at the end); the library
+    # records e0 before its first kernel, e1 and e2 around the step launches,
+    # e3 after the results' copy
+    dt, mass = grid.run(args.steps, CFL, events=(e0, e1, e2, e3), stream=sp)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -397,10 +391,7 @@ def run_ours(args):
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         grid.set_state(h_host, z_host, z_host, stream=sp)
-        dt2 = grid.cfl_dt(CFL, stream=sp)
-        grid.set_dt(dt2)
-        grid.step(args.steps, stream=sp)
-        mass2 = grid.mass(stream=sp)
+        dt2, mass2 = grid.run(args.steps, CFL, stream=sp)
         grid.get_state(out=out_host, stream=sp, sync=False)
         f1.record(stream)
         torch.cuda.synchronize()
@@ -465,7 +456,7 @@ def run_ours(args):
                         "planes), FP64 CFL dt, K steps, FP64 mass, device->host state; the state crosses "
                         "once per K-step job, so the bytes per step are the plane bytes / K; median of "
                         "three jobs (job_s)"},
-        "gpu_launches": int(launches) + 6,  # + CFL (4 launches) + mass (2)
+        "gpu_launches": int(launches) + 7,  # + CFL (4 launches) + coefficients (1) + mass (2)
         "clocks": clocks,
         "cpu_baseline": cpu,
         "checks": {"status": swe.strerror(status), "mass": mass, "mass_e2e": mass2, "dt": dt},

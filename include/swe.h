@@ -141,6 +141,24 @@ swe_status swe_mass(swe_ctx *ctx, double *mass_out, void *stream);
  */
 swe_status swe_cfl_dt(swe_ctx *ctx, double cfl, double *dt_out, void *stream);
 
+/*
+ * swe_run: one job of the Sec. 3 time loop without a host round trip inside:
+ * the FP64 CFL step of the current state (as swe_cfl_dt) is computed on the
+ * device and stays there, the n_steps >= 0 steps (as swe_step) take their
+ * coefficients from it, and the FP64 mass of the result (as swe_mass)
+ * follows.  Bit for bit the same dt, state and mass as swe_cfl_dt,
+ * swe_set_dt, swe_step and swe_mass in turn.  ``events`` (optional) is an
+ * array of four cudaEvent_t (as void*, each may be NULL) recorded on
+ * ``stream`` before the first kernel, before the first step launch, after
+ * the last step launch and after the results' copy to the host, so that the
+ * job's device time excludes host latency.  Synchronous: waits once, at the
+ * end, then sets the context's dt and writes *dt_out and *mass_out (either
+ * may be NULL).  Returns SWE_ECHECK (*dt_out = 0, the state left as it was)
+ * if some h <= 0 or is not finite.
+ */
+swe_status swe_run(swe_ctx *ctx, int n_steps, double cfl, double *dt_out, double *mass_out, void *const *events,
+                   void *stream);
+
 /* Synchronises ``stream`` and returns the device error word:
  * SWE_OK or SWE_ETIMEOUT (a kernel's bounded wait gave up); clears it. */
 swe_status swe_check(swe_ctx *ctx, void *stream);

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 
+#include "swe_device.cuh"
 #include "swe_internal.h"
 
 struct swe_ctx {
@@ -36,6 +37,7 @@ struct swe_ctx {
     double *result = nullptr;   // reduction results (device, 4 doubles)
     double *host_result = nullptr;  // pinned copy of result
     int *err = nullptr;          // device error word
+    void *kdev = nullptr;        // device DevCoef<T> (swe_run's step coefficients)
     long long launches = 0;
 };
 
@@ -165,6 +167,7 @@ void swe_destroy(swe_ctx *c)
     cudaFree(c->scratch);
     cudaFree(c->result);
     cudaFree(c->err);
+    cudaFree(c->kdev);
     cudaFreeHost(c->host_result);
     delete c;
 }
@@ -223,6 +226,7 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
         return fail(st);
     if ((st = cuda_status(cudaMalloc(&c->result, 4 * sizeof(double)))) != SWE_OK) return fail(st);
     if ((st = cuda_status(cudaMalloc(&c->err, sizeof(int)))) != SWE_OK) return fail(st);
+    if ((st = cuda_status(cudaMalloc(&c->kdev, sizeof(swe::DevCoef<double>)))) != SWE_OK) return fail(st);
     if ((st = cuda_status(cudaMemset(c->err, 0, sizeof(int)))) != SWE_OK) return fail(st);
     if ((st = cuda_status(cudaMallocHost(&c->host_result, 4 * sizeof(double)))) != SWE_OK) return fail(st);
 
@@ -316,16 +320,16 @@ swe_status swe_get_state(swe_ctx *c, void *h, void *hu, void *hv, long long ld, 
     return copy_planes(c, p, ld, false, static_cast<cudaStream_t>(stream));
 }
 
-swe_status swe_step(swe_ctx *c, int n_steps, void *stream)
+// n_steps steps of the context's kernel on stream s; kd (optional) is the
+// device DevCoef the kernels take their coefficients from instead of c->dt.
+static swe_status step_launches(swe_ctx *c, int n_steps, cudaStream_t s, const void *kd)
 {
-    if (!c || n_steps < 0) return SWE_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     int n = 0;
     if (c->kernel == SWE_KERNEL_TEMPORAL) {
         for (; n + 2 <= n_steps; n += 2) {
             const int in = c->cur, outb = c->cur ^ 1;
             cudaError_t e = launch_tb2(c->dtype, c->tb_variant, c->maps_tb[in], c->state[outb], c->plane, c->nx,
-                                       c->ny, c->pitch, c->dx, c->dy, c->dt, c->g, c->err, s);
+                                       c->ny, c->pitch, c->dx, c->dy, c->dt, c->g, c->err, s, kd);
             if (e != cudaSuccess) return cuda_status(e);
             c->cur = outb;
             c->launches += 1;
@@ -336,19 +340,25 @@ swe_status swe_step(swe_ctx *c, int n_steps, void *stream)
         cudaError_t e;
         if (c->kernel == SWE_KERNEL_PACKED) {
             e = launch_packed(&c->maps_pk[in], c->packed[outb], c->nx, c->ny, c->ppitch, c->dx, c->dy, c->dt, c->g,
-                              c->err, s);
+                              c->err, s, kd);
             c->planes_stale = true;
         } else if (c->kernel == SWE_KERNEL_NAIVE)
             e = launch_naive(c->dtype, c->state[in], c->state[outb], c->plane, c->nx, c->ny, c->pitch, c->dx, c->dy,
-                             c->dt, c->g, s);
+                             c->dt, c->g, s, kd);
         else
             e = launch_tiled(c->dtype, c->maps[in], c->state[outb], c->plane, c->nx, c->ny, c->pitch, c->dx, c->dy,
-                             c->dt, c->g, c->err, s);
+                             c->dt, c->g, c->err, s, kd);
         if (e != cudaSuccess) return cuda_status(e);
         c->cur = outb;
         c->launches += 1;
     }
     return SWE_OK;
+}
+
+swe_status swe_step(swe_ctx *c, int n_steps, void *stream)
+{
+    if (!c || n_steps < 0) return SWE_EINVAL;
+    return step_launches(c, n_steps, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 swe_status swe_mass(swe_ctx *c, double *mass_out, void *stream)
@@ -378,6 +388,46 @@ swe_status swe_cfl_dt(swe_ctx *c, double cfl, double *dt_out, void *stream)
         return SWE_ECHECK;
     }
     *dt_out = c->host_result[0];
+    return SWE_OK;
+}
+
+swe_status swe_run(swe_ctx *c, int n_steps, double cfl, double *dt_out, double *mass_out, void *const *events,
+                   void *stream)
+{
+    if (!c || n_steps < 0 || !finite_pos(cfl)) return SWE_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto mark = [&](int i) -> cudaError_t {
+        return events && events[i] ? cudaEventRecord(static_cast<cudaEvent_t>(events[i]), s) : cudaSuccess;
+    };
+    SWE_TRY(mark(0));
+    SWE_TRY(sync_planes(c, s));
+    // result[0..1] = (dt, bad cells), result[2] = mass
+    SWE_TRY(launch_cfl(c->dtype, plane_ptr(c, c->cur, 0), plane_ptr(c, c->cur, 1), plane_ptr(c, c->cur, 2), c->nx,
+                       c->ny, c->pitch, c->dx, c->dy, c->g, cfl, c->scratch, c->result, s));
+    SWE_TRY(launch_coef_from_cfl(c->dtype, c->result, c->dx, c->dy, c->g, c->kdev, s));
+    const int cur0 = c->cur;
+    const long long launches0 = c->launches;
+    SWE_TRY(mark(1));
+    const swe_status st = step_launches(c, n_steps, s, c->kdev);
+    if (st != SWE_OK) return st;
+    SWE_TRY(mark(2));
+    SWE_TRY(sync_planes(c, s));
+    SWE_TRY(launch_mass(c->dtype, plane_ptr(c, c->cur, 0), c->nx, c->ny, c->pitch, c->dx * c->dy, c->scratch,
+                        c->result + 2, s));
+    SWE_TRY(cudaMemcpyAsync(c->host_result, c->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SWE_TRY(mark(3));
+    SWE_TRY(cudaStreamSynchronize(s));
+    if (c->host_result[1] != 0.0) {
+        // the step kernels skipped: the state is still in the first buffer
+        c->cur = cur0;
+        c->launches = launches0;
+        c->planes_stale = false;
+        if (dt_out) *dt_out = 0.0;
+        return SWE_ECHECK;
+    }
+    c->dt = c->host_result[0];
+    if (dt_out) *dt_out = c->dt;
+    if (mass_out) *mass_out = c->host_result[2];
     return SWE_OK;
 }
 

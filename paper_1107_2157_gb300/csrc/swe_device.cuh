@@ -214,6 +214,27 @@ __host__ __device__ inline Coef<T> make_coef(double dx, double dy, double dt, do
     return k;
 }
 
+// Coefficients a step kernel can read from device memory instead of its
+// argument (swe_run): written on the device from the FP64 CFL step by the
+// same make_coef, so they have the host's bits.  skip != 0 when the CFL pass
+// found a non-positive depth; the step kernels then leave the state alone.
+template <typename T>
+struct DevCoef {
+    Coef<T> k;
+    int skip;
+};
+
+// Takes the device coefficients if kd is given; false when the step is to
+// be skipped.  Every thread of a kernel calls it before any barrier.
+template <typename T>
+__device__ __forceinline__ bool take_dev_coef(const DevCoef<T> *kd, Coef<T> &k)
+{
+    if (!kd) return true;
+    if (kd->skip) return false;
+    k = kd->k;
+    return true;
+}
+
 // A cell with its physical fluxes (Sec. 3 conservation laws):
 //   F = (U, U^2/H + g H^2/2, U V/H),  G = (V, U V/H, V^2/H + g H^2/2).
 // f3 doubles as G's second component (both are U V / H).

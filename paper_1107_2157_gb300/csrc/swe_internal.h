@@ -29,19 +29,22 @@ struct StepGeom {
 
 // Launchers implemented in swe_step.cu.  ``in``/``out`` each point to three
 // planes (H, U, V) of ``plane`` elements.  All return cudaError_t of the
-// launch.
+// launch.  ``kd``, if given, is a device DevCoef<T> (swe_device.cuh) whose
+// coefficients replace those made from (dx, dy, dt, g).
 cudaError_t launch_naive(int dtype, const void *in, void *out, size_t plane, int nx, int ny, long long pitch,
-                         double dx, double dy, double dt, double g, cudaStream_t s);
+                         double dx, double dy, double dt, double g, cudaStream_t s, const void *kd = nullptr);
 cudaError_t launch_tiled(int dtype, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
-                         long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+                         long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                         const void *kd = nullptr);
 cudaError_t launch_tb2(int dtype, int variant, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
-                       long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+                       long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                       const void *kd = nullptr);
 void tb2_box(int dtype, int variant, int *bw, int *bh);  // TMA box of two-step kernel shape ``variant``
 // Packed-state kernel (swe_packed.cu): state as (h, hu, hv, 0) float4 cells,
 // ppitch cells per row.  launch_pack copies the planes into the packed
 // buffer (unpack = false) or back (unpack = true).
 cudaError_t launch_packed(const CUtensorMap *map, void *out, int nx, int ny, long long ppitch, double dx, double dy,
-                          double dt, double g, int *err, cudaStream_t s);
+                          double dt, double g, int *err, cudaStream_t s, const void *kd = nullptr);
 cudaError_t launch_pack(const void *h, const void *u, const void *v, long long pitch, void *out, long long ppitch,
                         int nx, int ny, bool unpack, cudaStream_t s);
 void packed_box(int *bw, int *bh);  // TMA box (cells) of the packed kernel
@@ -73,6 +76,10 @@ cudaError_t launch_mass(int dtype, const void *H, int nx, int ny, long long pitc
 cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, int nx, int ny, long long pitch,
                        double dx, double dy, double g, double cfl, double *scratch, double *out_dev,
                        cudaStream_t s);
+// The step coefficients of a CFL result res_dev = (dt, bad-cell count) into
+// the device DevCoef<T> at kd (T the context's dtype); kd->skip when bad.
+cudaError_t launch_coef_from_cfl(int dtype, const double *res_dev, double dx, double dy, double g, void *kd,
+                                 cudaStream_t s);
 
 // TMA descriptor encoding through the driver entry point (no -lcuda link).
 // Encodes a 2D map over an nx x ny plane with the given box; returns false

@@ -16,8 +16,10 @@ constexpr size_t kPackedBoxBytes = (size_t)PackedCfg::BW * PackedCfg::BH * 16;
 constexpr size_t kPackedSmem = (kPackedBoxBytes + 127) / 128 * 128 + 128;
 
 __global__ void __launch_bounds__(128) lw_packed_kernel(const __grid_constant__ CUtensorMap m, float4 *__restrict__ out,
-                                                        int nx, int ny, long long ppitch, Coef<float> k, int *err)
+                                                        int nx, int ny, long long ppitch, Coef<float> k, int *err,
+                                                        const DevCoef<float> *kd)
 {
+    if (!take_dev_coef(kd, k)) return;
     using C = PackedCfg;
     constexpr int VX = C::VX;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -82,7 +84,7 @@ void packed_box(int *bw, int *bh)
 }
 
 cudaError_t launch_packed(const CUtensorMap *map, void *out, int nx, int ny, long long ppitch, double dx, double dy,
-                          double dt, double g, int *err, cudaStream_t s)
+                          double dt, double g, int *err, cudaStream_t s, const void *kd)
 {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
@@ -92,7 +94,8 @@ cudaError_t launch_packed(const CUtensorMap *map, void *out, int nx, int ny, lon
     if (attr != cudaSuccess) return attr;
     const Coef<float> k = make_coef<float>(dx, dy, dt, g);
     const dim3 grid((nx + PackedCfg::TX - 1) / PackedCfg::TX, (ny + PackedCfg::TY - 1) / PackedCfg::TY);
-    lw_packed_kernel<<<grid, 128, kPackedSmem, s>>>(*map, static_cast<float4 *>(out), nx, ny, ppitch, k, err);
+    lw_packed_kernel<<<grid, 128, kPackedSmem, s>>>(*map, static_cast<float4 *>(out), nx, ny, ppitch, k, err,
+                                                    static_cast<const DevCoef<float> *>(kd));
     return cudaGetLastError();
 }
 

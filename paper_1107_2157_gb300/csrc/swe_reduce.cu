@@ -542,6 +542,26 @@ cudaError_t launch_cfl_many(const RedGrid *grids_dev, int n, int B, double g, do
     return cudaGetLastError();
 }
 
+// Step coefficients on the device from a CFL result res = (dt, bad-cell
+// count) (swe_run): make_coef<T> in the host's FP64 operations, so the bits
+// are those the host would pass; skip is set when a cell was bad.
+template <typename T>
+__global__ void coef_from_cfl_kernel(const double *res, double dx, double dy, double g, DevCoef<T> *kd)
+{
+    kd->k = make_coef<T>(dx, dy, res[0], g);
+    kd->skip = res[1] != 0.0 ? 1 : 0;
+}
+
+cudaError_t launch_coef_from_cfl(int dtype, const double *res_dev, double dx, double dy, double g, void *kd,
+                                 cudaStream_t s)
+{
+    if (dtype == SWE_F64)
+        coef_from_cfl_kernel<double><<<1, 1, 0, s>>>(res_dev, dx, dy, g, static_cast<DevCoef<double> *>(kd));
+    else
+        coef_from_cfl_kernel<float><<<1, 1, 0, s>>>(res_dev, dx, dy, g, static_cast<DevCoef<float> *>(kd));
+    return cudaGetLastError();
+}
+
 }  // namespace swe
 
 // ---------------------------------------------------------------------------

@@ -27,8 +27,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) lw_naive_kernel(const T *__restrict__ H, const T *__restrict__ U,
                                                        const T *__restrict__ V, T *__restrict__ oH,
                                                        T *__restrict__ oU, T *__restrict__ oV, int nx, int ny,
-                                                       long long pitch, Coef<T> k)
+                                                       long long pitch, Coef<T> k, const DevCoef<T> *kd)
 {
+    if (!take_dev_coef(kd, k)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
@@ -60,8 +61,10 @@ __global__ void __launch_bounds__(NWARP * 32) lw_tiled_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap mV,
                                                               T *__restrict__ oH, T *__restrict__ oU,
                                                               T *__restrict__ oV, int nx, int ny,
-                                                              long long pitch, Coef<T> k, int *err)
+                                                              long long pitch, Coef<T> k, int *err,
+                                                              const DevCoef<T> *kd)
 {
+    if (!take_dev_coef(kd, k)) return;
     using C = TiledCfg<T, NWARP, RY>;
     extern __shared__ __align__(128) unsigned char smem[];
     T *sH = reinterpret_cast<T *>(smem);
@@ -113,7 +116,7 @@ void tiled_box(int dtype, int *bw, int *bh)
 }
 
 cudaError_t launch_naive(int dtype, const void *in, void *out, size_t plane, int nx, int ny, long long pitch,
-                         double dx, double dy, double dt, double g, cudaStream_t s)
+                         double dx, double dy, double dt, double g, cudaStream_t s, const void *kd)
 {
     const dim3 block(64, 4);
     const dim3 grid((nx + 63) / 64, (ny + 3) / 4);
@@ -121,12 +124,14 @@ cudaError_t launch_naive(int dtype, const void *in, void *out, size_t plane, int
         const double *a = static_cast<const double *>(in);
         double *b = static_cast<double *>(out);
         lw_naive_kernel<double><<<grid, block, 0, s>>>(a, a + plane, a + 2 * plane, b, b + plane, b + 2 * plane, nx,
-                                                       ny, pitch, make_coef<double>(dx, dy, dt, g));
+                                                       ny, pitch, make_coef<double>(dx, dy, dt, g),
+                                                       static_cast<const DevCoef<double> *>(kd));
     } else {
         const float *a = static_cast<const float *>(in);
         float *b = static_cast<float *>(out);
         lw_naive_kernel<float><<<grid, block, 0, s>>>(a, a + plane, a + 2 * plane, b, b + plane, b + 2 * plane, nx,
-                                                      ny, pitch, make_coef<float>(dx, dy, dt, g));
+                                                      ny, pitch, make_coef<float>(dx, dy, dt, g),
+                                                      static_cast<const DevCoef<float> *>(kd));
     }
     return cudaGetLastError();
 }
@@ -134,7 +139,7 @@ cudaError_t launch_naive(int dtype, const void *in, void *out, size_t plane, int
 template <typename T, typename Cfg>
 static cudaError_t launch_tiled_t(const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
                                   long long pitch, double dx, double dy, double dt, double g, int *err,
-                                  cudaStream_t s)
+                                  cudaStream_t s, const void *kd)
 {
     auto kern = lw_tiled_kernel<T, kTiledWarps, kTiledRows>;
     static std::once_flag once;
@@ -146,16 +151,18 @@ static cudaError_t launch_tiled_t(const CUtensorMap *maps, void *out, size_t pla
     T *b = static_cast<T *>(out);
     const dim3 grid((nx + Cfg::TX - 1) / Cfg::TX, (ny + Cfg::TY - 1) / Cfg::TY);
     kern<<<grid, kTiledWarps * 32, Cfg::SMEM, s>>>(maps[0], maps[1], maps[2], b, b + plane, b + 2 * plane, nx, ny,
-                                                   pitch, make_coef<T>(dx, dy, dt, g), err);
+                                                   pitch, make_coef<T>(dx, dy, dt, g), err,
+                                                   static_cast<const DevCoef<T> *>(kd));
     return cudaGetLastError();
 }
 
 cudaError_t launch_tiled(int dtype, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
-                         long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s)
+                         long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                         const void *kd)
 {
     if (dtype == SWE_F64)
-        return launch_tiled_t<double, CfgD>(maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
-    return launch_tiled_t<float, CfgF>(maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
+        return launch_tiled_t<double, CfgD>(maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+    return launch_tiled_t<float, CfgF>(maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
 }
 
 }  // namespace swe

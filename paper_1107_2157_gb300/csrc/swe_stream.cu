@@ -394,8 +394,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     lw_stream_kernel(const __grid_constant__ CUtensorMap mH, const __grid_constant__ CUtensorMap mU,
                      const __grid_constant__ CUtensorMap mV, float *__restrict__ oH, float *__restrict__ oU,
                      float *__restrict__ oV, int nx, int ny, long long pitch, int K, int Ke, Coef<float> k,
-                     int *err)
+                     int *err, const DevCoef<float> *kd)
 {
+    if (!take_dev_coef(kd, k)) return;
     using C = StreamCfg<VP, LO, NO, CR, NSLOT, WARPS>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -496,7 +497,8 @@ bool stream_box(int variant, int *bw, int *bh)
 
 template <int V>
 static cudaError_t launch_stream_t(const CUtensorMap *maps, void *out, size_t plane, int nx, int ny, long long pitch,
-                                   double dx, double dy, double dt, double g, int *err, cudaStream_t s)
+                                   double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                                   const void *kd)
 {
     using S = StreamShape<V>;
     using C = StreamCfgOf<V>;
@@ -526,18 +528,20 @@ static cudaError_t launch_stream_t(const CUtensorMap *maps, void *out, size_t pl
     const int grid = (K * ns + ne * (Ke - K) + S::WARPS - 1) / S::WARPS;
     float *b = static_cast<float *>(out);
     kern<<<grid, S::WARPS * 32, C::SMEM, s>>>(maps[0], maps[1], maps[2], b, b + plane, b + 2 * plane, nx, ny,
-                                                   pitch, K, Ke, make_coef<float>(dx, dy, dt, g), err);
+                                                   pitch, K, Ke, make_coef<float>(dx, dy, dt, g), err,
+                                                   static_cast<const DevCoef<float> *>(kd));
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream(int variant, const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
-                          long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s)
+                          long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                          const void *kd)
 {
     switch (variant) {
-        case 5: return launch_stream_t<5>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
-        case 6: return launch_stream_t<6>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
-        case 7: return launch_stream_t<7>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
-        case 8: return launch_stream_t<8>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
+        case 5: return launch_stream_t<5>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+        case 6: return launch_stream_t<6>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+        case 7: return launch_stream_t<7>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+        case 8: return launch_stream_t<8>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(NWARP * 32) lw_tb2_kernel(const __grid_constan
                                                             const __grid_constant__ CUtensorMap mV,
                                                             T *__restrict__ oH, T *__restrict__ oU,
                                                             T *__restrict__ oV, int nx, int ny, long long pitch,
-                                                            Coef<T> k, int *err)
+                                                            Coef<T> k, int *err, const DevCoef<T> *kd)
 {
+    if (!take_dev_coef(kd, k)) return;
     using B = Tb2Cfg<T, NWARP, RY>;
     using C = typename B::C;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -91,7 +92,8 @@ static void tb2_box_t(int *bw, int *bh)
 
 bool stream_box(int variant, int *bw, int *bh);
 cudaError_t launch_stream(int variant, const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
-                          long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s);
+                          long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                          const void *kd);
 
 void tb2_box(int dtype, int variant, int *bw, int *bh)
 {
@@ -108,7 +110,8 @@ void tb2_box(int dtype, int variant, int *bw, int *bh)
 
 template <typename T, typename S>
 static cudaError_t launch_tb2_t(const CUtensorMap *maps, void *out, size_t plane, int nx, int ny, long long pitch,
-                                double dx, double dy, double dt, double g, int *err, cudaStream_t s, bool persistent)
+                                double dx, double dy, double dt, double g, int *err, cudaStream_t s, bool persistent,
+                                const void *kd)
 {
     using Cfg = typename S::Cfg;
     auto kern = lw_tb2_kernel<T, S::WARPS, S::ROWS>;
@@ -133,30 +136,33 @@ static cudaError_t launch_tb2_t(const CUtensorMap *maps, void *out, size_t plane
         (long long)((nx + Cfg::C::TX - 1) / Cfg::C::TX) * (long long)((ny + Cfg::C::TY - 1) / Cfg::C::TY);
     const int grid = (int)(persistent ? std::min<long long>(tiles, ctas) : tiles);
     kern<<<grid, S::WARPS * 32, Cfg::SMEM, s>>>(maps[0], maps[1], maps[2], b, b + plane, b + 2 * plane, nx, ny,
-                                                pitch, make_coef<T>(dx, dy, dt, g), err);
+                                                pitch, make_coef<T>(dx, dy, dt, g), err,
+                                                static_cast<const DevCoef<T> *>(kd));
     return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_tb2_v(int variant, const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
-                                long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s)
+                                long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                                const void *kd)
 {
     switch (variant) {
-        case 1: return launch_tb2_t<T, TbShape<T, 8, 4>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false);
-        case 2: return launch_tb2_t<T, TbShape<T, 4, 4>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false);
-        case 3: return launch_tb2_t<T, TbShape<T, 8, 2>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false);
-        case 4: return launch_tb2_t<T, TbShape<T, 8, 4>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, true);
-        default: return launch_tb2_t<T, TbShape<T, 4, 8>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false);
+        case 1: return launch_tb2_t<T, TbShape<T, 8, 4>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false, kd);
+        case 2: return launch_tb2_t<T, TbShape<T, 4, 4>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false, kd);
+        case 3: return launch_tb2_t<T, TbShape<T, 8, 2>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false, kd);
+        case 4: return launch_tb2_t<T, TbShape<T, 8, 4>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, true, kd);
+        default: return launch_tb2_t<T, TbShape<T, 4, 8>>(maps, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, false, kd);
     }
 }
 
 cudaError_t launch_tb2(int dtype, int variant, const CUtensorMap *maps_in, void *out, size_t plane, int nx, int ny,
-                       long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s)
+                       long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                       const void *kd)
 {
     if (dtype == SWE_F64)
-        return launch_tb2_v<double>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
-    if (variant >= 5) return launch_stream(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
-    return launch_tb2_v<float>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s);
+        return launch_tb2_v<double>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+    if (variant >= 5) return launch_stream(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+    return launch_tb2_v<float>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
 }
 
 }  // namespace swe

@@ -58,6 +58,7 @@ _SIGS = {
     "swe_step": (_i, [_vp, _i, _vp]),
     "swe_mass": (_i, [_vp, ctypes.POINTER(_d), _vp]),
     "swe_cfl_dt": (_i, [_vp, _d, ctypes.POINTER(_d), _vp]),
+    "swe_run": (_i, [_vp, _i, _d, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_vp), _vp]),
     "swe_check": (_i, [_vp, _vp]),
     "swe_query": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "swe_strerror": (ctypes.c_char_p, [_i]),
@@ -207,6 +208,24 @@ def swe_cfl_dt(ctx, cfl, stream=None) -> float:
     return d.value
 
 
+def swe_run(ctx, n_steps, cfl, events=None, stream=None):
+    """CFL dt, n_steps steps and the mass in one call (see include/swe.h);
+    ``events``: optional four torch.cuda.Event (or None) recorded before the
+    job, around the step launches and after the results' copy.  Returns
+    (dt, mass)."""
+    d, m = _d(), _d()
+    ev = None
+    if events is not None:
+        # torch creates a CUDA event at its first record; swe_run records it
+        # again at its place on ``stream``
+        for e in events:
+            if e is not None:
+                e.record()
+        ev = (_vp * 4)(*[None if e is None else e.cuda_event for e in events])
+    check(lib().swe_run(ctx, int(n_steps), cfl, ctypes.byref(d), ctypes.byref(m), ev, stream), "swe_run")
+    return d.value, m.value
+
+
 def swe_check(ctx, stream=None) -> int:
     return int(lib().swe_check(ctx, stream))
 
@@ -322,6 +341,11 @@ class Grid:
 
     def cfl_dt(self, cfl, stream=None):
         return swe_cfl_dt(self.ctx, cfl, stream if stream is not None else current_stream())
+
+    def run(self, n, cfl, events=None, stream=None):
+        """The FP64 CFL dt, n steps with it and the FP64 mass, with one host
+        synchronisation (swe_run); returns (dt, mass)."""
+        return swe_run(self.ctx, n, cfl, events, stream if stream is not None else current_stream())
 
     def check(self, stream=None):
         return swe_check(self.ctx, stream if stream is not None else current_stream())

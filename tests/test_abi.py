@@ -140,3 +140,11 @@ def test_more_entry_points_reject_bad_arguments_before_device_work(libswe):
     rs = libswe.swe_resample
     rs.argtypes = [c_void_p, c_ll, c_ll, c_ll, c_int, c_int, c_void_p, c_ll, c_ll, c_ll, c_int, c_int, c_int, c_void_p]
     assert rs(fake, 0, 0, 256, 256, 256, fake, 0, 0, 512, 512, 512, 1, None) == EINVAL  # upsampling
+
+    run = libswe.swe_run
+    run.argtypes = [c_void_p, c_int, c_double, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                    ctypes.POINTER(c_void_p), c_void_p]
+    d = c_double()
+    assert run(None, 2, 0.2, ctypes.byref(d), None, None, None) == EINVAL   # no context
+    assert run(fake, -1, 0.2, ctypes.byref(d), None, None, None) == EINVAL  # negative step count
+    assert run(fake, 2, 0.0, ctypes.byref(d), None, None, None) == EINVAL   # CFL number not positive

@@ -494,6 +494,66 @@ def test_two_step_defaults_and_fp32_only_shapes():
         assert e.value.status == 6  # SWE_EUNSUPPORTED
 
 
+@pytest.mark.parametrize("dtype,kernel,variant", [("f32", 1, None), ("f32", 2, None), ("f32", 3, None),
+                                                   ("f32", 3, 4), ("f32", 4, None), ("f64", 2, None),
+                                                   ("f64", 3, None)])
+@pytest.mark.parametrize("steps", [0, 1, 6, 7])
+def test_run_equals_cfl_step_and_mass_in_turn(dtype, kernel, variant, steps):
+    """swe_run keeps the CFL step on the device and the step kernels read
+    their coefficients from there: the dt, the state and the mass are those
+    of swe_cfl_dt, swe_set_dt, swe_step and swe_mass in turn, bit for bit,
+    for every kernel and an even or odd step count."""
+    import torch
+    from paper_1107_2157_gb300 import Grid
+    nx, ny = 389, 263
+    npd = np.float32 if dtype == "f32" else np.float64
+    s = si.smooth_flow_state(71, nx, ny).rounded_to(npd)
+    planes = [np.ascontiguousarray(a, npd) for a in (s.h, s.hu, s.hv)]
+    with Grid(nx, ny, 0.8, 1.1, 0.01, G, dtype=dtype, kernel=kernel, variant=variant) as a:
+        a.set_state(*planes)
+        dt = a.cfl_dt(0.3)
+        a.set_dt(dt)
+        a.step(steps)
+        m = a.mass()
+        ref = a.get_state()
+    with Grid(nx, ny, 0.8, 1.1, 0.01, G, dtype=dtype, kernel=kernel, variant=variant) as b:
+        b.set_state(*planes)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        dt2, m2 = b.run(steps, 0.3, events=ev)
+        got = b.get_state()
+        assert b.check() == 0
+        t = [ev[0].elapsed_time(e) for e in ev[1:]]
+        assert 0.0 <= t[0] <= t[1] <= t[2], t
+    assert dt2 == dt and m2 == m
+    for k in range(3):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_run_leaves_the_state_alone_on_a_bad_depth():
+    """A cell with h = 0: swe_run returns SWE_ECHECK with dt 0, the step
+    kernels skip, and the state reads back unchanged; a good state run
+    afterwards on the same context steps normally."""
+    from paper_1107_2157_gb300 import Grid, SweError
+    nx, ny = 300, 130
+    s = si.smooth_flow_state(5, nx, ny).rounded_to(np.float32)
+    h = np.ascontiguousarray(s.h, np.float32)
+    h[40, 77] = 0.0
+    planes = [h] + [np.ascontiguousarray(a, np.float32) for a in (s.hu, s.hv)]
+    with Grid(nx, ny, 1.0, 1.0, 0.01, G, dtype="f32") as grid:
+        grid.set_state(*planes)
+        with pytest.raises(SweError) as e:
+            grid.run(7, 0.2)
+        assert e.value.status == 5  # SWE_ECHECK
+        got = grid.get_state()
+        for k in range(3):
+            assert np.array_equal(got[k], planes[k]), k
+        h[40, 77] = 1.0
+        grid.set_state(*planes)
+        dt, m = grid.run(7, 0.2)
+        assert dt == oracle.cfl_dt(h.astype(np.float64), s.hu, s.hv, 1.0, 1.0, G, 0.2)
+        assert not np.array_equal(grid.get_state()[0], h)
+
+
 def test_fp32_mass_is_the_exact_sum_on_awkward_data():
     """The FP32 mass sums the depths exactly in 64-bit integers (flushing to
     FP64 only when the largest exponent rises): on depths within a few
