@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="ensemble: default kernel variant, no autotuning")
     p.add_argument("--ensemble-variant", type=int, default=None,
                    help="ensemble: this kernel variant at 2 CTAs/SM (or fewer if it does not fit), no autotuning")
+    p.add_argument("--ensemble-ctas", type=int, default=2,
+                   help="ensemble: CTAs per SM with --ensemble-variant (fewer if they do not fit)")
     p.add_argument("--skip-train", action="store_true",
                    help="learned: serve with untrained weights (kernel timing and profiling only)")
     p.add_argument("--tune-cache", default=None)
@@ -130,8 +132,8 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "lw_tb2_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_temporal.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
                              "paper_1107_2157_gb300/csrc/swe_device.cuh"),
-    "lw_stream_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_stream.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
-                                "paper_1107_2157_gb300/csrc/swe_device.cuh"),
+    "lw_stream_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_stream.cu", "paper_1107_2157_gb300/csrc/swe_stream.cuh",
+                                "paper_1107_2157_gb300/csrc/swe_tile.cuh", "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "region_lw_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_region.cu", "paper_1107_2157_gb300/csrc/swe_region.cuh",
                                 "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "region_lw_kernel<float, bed>": ("paper_1107_2157_gb300/csrc/swe_region.cu",
@@ -500,8 +502,11 @@ def ensemble_record(args, steps=500):
         t = e0.elapsed_time(e1) / 1e3
         rc, flags = b.status(stream=sp)
         depth = int(b.query(swe.SWE_BQ_DEPTH))
+        kind = int(b.query(swe.SWE_BQ_KIND))
         tuned = {k: int(b.query(getattr(swe, "SWE_BQ_" + k))) for k in ("VARIANT", "CTAS_PER_SM", "TILE_X",
                                                                           "TILE_Y", "STAGES", "DEPTH")}
+        tuned["kernel"] = "batch_stream_kernel" if kind == 1 else ("batch_tb2_kernel" if depth == 2
+                                                                     else "batch_lw_kernel")
     peak, kind = measured_peaks()
     rate = cells * steps / t
     bpu = BYTES_PER_CELL_F32 / depth
@@ -586,7 +591,7 @@ def run_ensemble(args):
         b.set_dt(dts, stream=sp)
         t0 = time.perf_counter()
         if args.ensemble_variant is not None:
-            b.configure(args.ensemble_variant, 2)
+            b.configure(args.ensemble_variant, args.ensemble_ctas)
         elif not args.no_tune:
             b.tune(args.tune_cache, stream=sp)
         t_tune = time.perf_counter() - t0
@@ -608,19 +613,23 @@ def run_ensemble(args):
         t = e0.elapsed_time(e1) / 1e3
         q = {k: b.query(getattr(swe, k)) for k in ("SWE_BQ_VARIANT", "SWE_BQ_CTAS_PER_SM", "SWE_BQ_TILE_X",
                                                    "SWE_BQ_TILE_Y", "SWE_BQ_STAGES", "SWE_BQ_GRAPH",
-                                                   "SWE_BQ_TILES", "SWE_BQ_BLOCKS")}
+                                                   "SWE_BQ_TILES", "SWE_BQ_BLOCKS", "SWE_BQ_DEPTH", "SWE_BQ_KIND")}
+        q["kernel"] = "batch_stream_kernel" if q["SWE_BQ_KIND"] == 1 else (
+            "batch_tb2_kernel" if q["SWE_BQ_DEPTH"] == 2 else "batch_lw_kernel")
         m = b.mass(stream=sp)
         b.close()
     peak, kind = measured_peaks()
     rate = cells * args.steps / t
+    bpu = BYTES_PER_CELL_F32 / q["SWE_BQ_DEPTH"]
     line = {"metric": METRIC, "workload": "ensemble", "value": rate, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%d instances, nx, ny uniform in [64, 1024] (seed 2), 4 bumps each, "
                                    "per-instance FP64 CFL 0.2 dt, one persistent launch per job" % n,
                        "cells": cells},
-            "roofline": {"bound": "hbm", "achieved": BYTES_PER_CELL_F32 * rate / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": BYTES_PER_CELL_F32 * rate / 1e9 / peak},
+            # the state read and written once per pass: 24 B per cell, per step or per two steps
+            "roofline": {"bound": "hbm", "achieved": bpu * rate / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bpu * rate / 1e9 / peak, "algorithmic_bytes_per_cell_update": bpu},
             "tuned": q, "tune_s": t_tune, "ic_s": t_ic, "status": int(rc),
             "flags_set": int((flags != 0).sum()), "clocks": clocks, "mass_min": float(m.min())}
     print(json.dumps(line), flush=True)

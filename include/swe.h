@@ -316,7 +316,10 @@ swe_status swe_batch_copy_states(swe_batch *b, float *dst, void *stream);
 /* Selects a kernel variant (0 .. the count swe_batch_query reports for
  * SWE_BQ_VARIANT_COUNT, minus 1) and CTAs per SM explicitly (tests, tuning,
  * profiling); a CTA count above what fits is
- * lowered to it.  Synchronous; call it with no step of this batch in
+ * lowered to it.  Variants: 0..4 one step per pass over tiles (128 x 16..64,
+ * 4 or 8 warps, one or two TMA stages); 5..7 two steps per pass over tiles;
+ * 8, 9 two steps per pass by warps streaming up 120-column strips (3 and 2
+ * CTAs per SM).  Synchronous; call it with no step of this batch in
  * flight, since it rewrites the tile list the kernel reads.  SWE_EINVAL for
  * a variant out of range or ctas_per_sm < 1, SWE_EUNSUPPORTED if the
  * variant cannot run on this device. */
@@ -329,7 +332,8 @@ typedef enum {
     SWE_BQ_LAUNCHES = 9,     /* persistent launches enqueued so far */
     SWE_BQ_TUNED = 10,       /* 0 default, 1 tuned by timing, 2 from cache */
     SWE_BQ_CELLS = 11,       /* total cells over all instances */
-    SWE_BQ_VARIANT_COUNT = 12
+    SWE_BQ_VARIANT_COUNT = 12,
+    SWE_BQ_KIND = 13         /* the variant's kernel: 0 tiles (batch_lw / batch_tb2), 1 streaming warps */
 } swe_batch_query_key;
 swe_status swe_batch_query(swe_batch *b, int key, long long *value);
 

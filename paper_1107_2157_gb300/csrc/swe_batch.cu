@@ -12,6 +12,10 @@
 // the single-grid kernel (swe_tile.cuh).  A grid-wide barrier with a bounded
 // wait separates the time steps; all instances step together.
 //
+// Streaming variants (two steps per pass): warps stream up 120-column strips
+// of the instances as the single-grid default does (swe_stream.cuh), taking
+// (instance, strip, row range) segments longest first from a pass counter.
+//
 // The launch is captured once per (step count, buffer parity) into a CUDA
 // graph on a private stream and replayed on the caller's stream.  Tile shape,
 // staging depth and CTAs per SM come from the autotuner (swe_batch_tune),
@@ -31,6 +35,7 @@
 #include <utility>
 #include <vector>
 
+#include "swe_stream.cuh"
 #include "swe_tile.cuh"
 #include "swe_views.cuh"
 
@@ -224,6 +229,87 @@ __global__ void __launch_bounds__(NWARP * 32) batch_tb2_kernel(const BatchInst *
 }
 
 // ---------------------------------------------------------------------------
+// Two steps per pass by streaming warps (stream_segment, swe_stream.cuh):
+// every instance is cut into column strips and the strips into row ranges;
+// in every pass the warps take these segments, longest first, from a shared
+// counter, one step in the last pass of an odd count.  The work buffer holds
+// two pass counters (zeroed before each launch; pass p counts on p & 1 and
+// resets the other for pass p + 1) and then the segments.
+// ---------------------------------------------------------------------------
+struct SegRec {
+    int inst;
+    int strip;  // column strip: columns strip * OUT ..
+    int ya, yb; // output rows [ya, yb)
+};
+constexpr int kWorkHead = 4;  // ints before the segments: two counters, padded to 16 bytes
+static_assert(sizeof(SegRec) == 4 * sizeof(int), "segments are four ints");
+
+template <int VP, int LO, int NO, int CR, int NSLOT, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+    batch_stream_kernel(const BatchInst *__restrict__ inst, const CUtensorMap *__restrict__ maps, void *work,
+                        int nsegs, int n_steps, int parity0, GridBarrier *gbar, int *err, int *flags)
+{
+    using C = StreamCfg<VP, LO, NO, CR, NSLOT, WARPS>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StreamWarp<VP, LO, NO, CR, NSLOT, WARPS> w;
+    w.ring = smem + (size_t)warp * C::WARP_BYTES;
+    w.bars = reinterpret_cast<uint64_t *>(smem + WARPS * C::WARP_BYTES) + warp * NSLOT;
+    w.phase = 0;
+    w.err = err;
+    if (lane == 0) {
+        for (int i = 0; i < NSLOT; ++i) mbar_init(w.bars + i, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    int *ctr = static_cast<int *>(work);
+    const SegRec *segs = reinterpret_cast<const SegRec *>(ctr + kWorkHead);
+    bool ok = true;
+    int cur = parity0;
+    const int pairs = n_steps / 2, passes = pairs + (n_steps & 1);
+    for (int p = 0; p < passes; ++p, cur ^= 1) {
+        const bool two = p < pairs;
+        // the next pass's counter was last used two passes ago
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(p + 1) & 1] = 0;
+        // other warps' stores of the last pass -> this warp's TMA reads
+        if (lane == 0) fence_proxy_async_global();
+        for (;;) {
+            int i = 0;
+            if (lane == 0) i = atomicAdd(ctr + (p & 1), 1);
+            i = __shfl_sync(kFull, i, 0);
+            if (i >= nsegs || !ok) break;
+            const SegRec r = segs[i];
+            const BatchInst *I = inst + r.inst;
+            const CUtensorMap *m = maps + ((size_t)r.inst * 2 + cur) * 3;
+            w.mH = m;
+            w.mU = m + 1;
+            w.mV = m + 2;
+            float *o = I->buf[cur ^ 1];
+            const long long plane = I->plane, pitch = I->pitch;
+            const int nx = I->nx, ny = I->ny;
+            const Coef2 k2 = coef2(I->k);
+            const int xs = r.strip * C::OUT;
+            // Every strip takes the wall code path (the ghost patch changes
+            // nothing where no ghost column is in reach).  With instances a
+            // few strips wide, about 40 % of the strips hold a wall; one copy
+            // of the row loop instead of two cuts instruction-fetch stalls
+            // and spills and measured 18 % faster (0.468 against 0.568 ms per
+            // step on the 512-grid ensemble at 3 CTAs/SM).
+            bool bad = false;
+            float *oh = o, *ou = o + plane, *ov = o + 2 * plane;
+            if (two)
+                ok = stream_segment<true>(w, oh, ou, ov, nx, ny, pitch, xs, r.ya, r.yb, k2, bad);
+            else  // the one-step pass: an odd count's last
+                ok = stream_segment<true, VP, LO, NO, CR, NSLOT, WARPS, true>(w, oh, ou, ov, nx, ny, pitch, xs, r.ya,
+                                                                              r.yb, k2, bad);
+            if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags[r.inst], SWE_FLAG_NONPOSITIVE);
+        }
+        // every warp reaches the barrier, also after a timed-out wait
+        if (!grid_sync_bounded(gbar, gridDim.x, err)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Variants the autotuner chooses from
 // ---------------------------------------------------------------------------
 struct Variant {
@@ -231,6 +317,7 @@ struct Variant {
     int tile_x, tile_y, box_w, box_h;
     size_t smem;
     const void *func;
+    int kind = 0;  // 0: tiles (tile list), 1: streaming warps (segment schedule)
 };
 
 template <int NWARP, int RY, int STAGES>
@@ -251,6 +338,19 @@ static Variant make_variant_tb2()
                    reinterpret_cast<const void *>(&batch_tb2_kernel<NWARP, RY>)};
 }
 
+// Streaming warps: two pairs per lane, 120-column strips, two 4-row chunks,
+// 4 warps per CTA, registers for 3 CTAs per SM (as the single-grid default).
+using BatchStreamC = StreamCfg<2, 1, 30, 4, 2, 4>;
+template <int MINB>
+static Variant make_variant_stream()
+{
+    using C = BatchStreamC;
+    Variant v{4, C::ROWS, 2, 2, C::OUT, 0, C::BW, C::ROWS, C::SMEM,
+              reinterpret_cast<const void *>(&batch_stream_kernel<2, 1, 30, 4, 2, 4, MINB>)};
+    v.kind = 1;
+    return v;
+}
+
 // Buffer swaps (= launches of a step pass) that n steps take with a variant.
 static int swaps_of(const Variant &V, int n) { return V.depth == 2 ? n / 2 + (n & 1) : n; }
 
@@ -265,6 +365,8 @@ static const std::vector<Variant> &variants()
         make_variant_tb2<8, 4>(),  // two steps per pass: 128x32 tiles, 8 warps
         make_variant_tb2<4, 4>(),  // two steps per pass: 128x16 tiles
         make_variant_tb2<8, 2>(),  // two steps per pass: 128x16 tiles, 8 warps
+        make_variant_stream<3>(),  // two steps per pass: streaming warps, 120-column strips, 3 CTAs/SM
+        make_variant_stream<2>(),  // the same without the register cap (2 CTAs/SM)
     };
     return v;
 }
@@ -315,9 +417,12 @@ struct swe_batch {
     std::vector<BatchInst> h_inst;
     BatchInst *d_inst = nullptr;
     CUtensorMap *d_maps = nullptr;               // maps of the configured variant
-    std::map<int, CUtensorMap *> maps_by_box_h;  // written once each, never rewritten
+    std::map<int, CUtensorMap *> maps_by_box;  // by box (w, h); written once each, never rewritten
     TileRec *d_tiles = nullptr;
     int ntiles = 0, tiles_ty = -1, tiles_cap = 0;
+    void *d_work = nullptr;  // streaming variant: pass counters + segments
+    size_t work_cap = 0;     // bytes
+    int nwork = 0;           // segments
     GridBarrier *d_bar = nullptr;
     int *d_err = nullptr;
     int *d_flags = nullptr;
@@ -384,10 +489,46 @@ static void drop_graphs(swe_batch *b)
 
 // (Re)builds the tile list and tensor maps for variant v and sets the launch
 // width; invalidates captured graphs.
+// The streaming variant's segments for P warps: each instance's strips
+// (OUT columns, all on the same code path, so a row costs the same
+// everywhere) are cut into row ranges of about equal length, about four per
+// warp, and listed longest first: the warps take them in this order from
+// the pass counter.
+static swe_status build_stream_schedule(swe_batch *b, int P)
+{
+    constexpr int OUT = BatchStreamC::OUT, kMinRows = 16;
+    long long total = 0;
+    for (int i = 0; i < b->n; ++i) total += (long long)((b->nx[i] + OUT - 1) / OUT) * b->ny[i];
+    const double target = std::max(1.0, (double)total / (4.0 * P));
+    std::vector<SegRec> segs;
+    for (int i = 0; i < b->n; ++i) {
+        const int ns = (b->nx[i] + OUT - 1) / OUT, ny = b->ny[i];
+        const int K = std::max(1, std::min((int)std::lround(ny / target), std::max(1, ny / kMinRows)));
+        for (int st = 0; st < ns; ++st)
+            for (int j = 0; j < K; ++j)
+                segs.push_back(SegRec{i, st, (int)((long long)j * ny / K), (int)((long long)(j + 1) * ny / K)});
+    }
+    std::stable_sort(segs.begin(), segs.end(),
+                     [](const SegRec &a, const SegRec &c) { return a.yb - a.ya > c.yb - c.ya; });
+    std::vector<int> buf(kWorkHead + 4 * segs.size(), 0);
+    std::memcpy(buf.data() + kWorkHead, segs.data(), segs.size() * sizeof(SegRec));
+    const size_t bytes = buf.size() * sizeof(int);
+    if (bytes > b->work_cap) {
+        cudaFree(b->d_work);
+        b->d_work = nullptr;
+        b->work_cap = 0;
+        B_TRY(cudaMalloc(&b->d_work, bytes));
+        b->work_cap = bytes;
+    }
+    B_TRY(cudaMemcpy(b->d_work, buf.data(), bytes, cudaMemcpyHostToDevice));
+    b->nwork = (int)segs.size();
+    return SWE_OK;
+}
+
 static swe_status configure(swe_batch *b, int v, int ctas_per_sm)
 {
     const Variant &V = variants()[v];
-    if (b->tiles_ty != V.tile_y) {
+    if (V.kind == 0 && b->tiles_ty != V.tile_y) {
         std::vector<TileRec> t;
         for (int i = 0; i < b->n; ++i) {
             const int tx = (b->nx[i] + V.tile_x - 1) / V.tile_x;
@@ -408,8 +549,9 @@ static swe_status configure(swe_batch *b, int v, int ctas_per_sm)
     // Tensor maps live in global memory.  The TMA unit may keep a descriptor
     // cached by address, so a map array is never rewritten in place: each
     // box height gets its own array, encoded once.
-    auto found = b->maps_by_box_h.find(V.box_h);
-    if (found == b->maps_by_box_h.end()) {
+    const int box_key = V.box_w * 65536 + V.box_h;
+    auto found = b->maps_by_box.find(box_key);
+    if (found == b->maps_by_box.end()) {
         std::vector<CUtensorMap> m((size_t)b->n * 6);
         for (int i = 0; i < b->n; ++i)
             for (int c = 0; c < 2; ++c)
@@ -426,7 +568,7 @@ static swe_status configure(swe_batch *b, int v, int ctas_per_sm)
             cudaFree(d);
             return st_of(e);
         }
-        found = b->maps_by_box_h.emplace(V.box_h, d).first;
+        found = b->maps_by_box.emplace(box_key, d).first;
     }
     b->d_maps = found->second;
     B_TRY(cudaFuncSetAttribute(V.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem));
@@ -436,6 +578,10 @@ static swe_status configure(swe_batch *b, int v, int ctas_per_sm)
     b->variant = v;
     b->ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
     b->blocks = b->sms * b->ctas_per_sm;
+    if (V.kind == 1) {
+        const swe_status st = build_stream_schedule(b, b->blocks * V.nwarp);
+        if (st != SWE_OK) return st;
+    }
     drop_graphs(b);
     return SWE_OK;
 }
@@ -462,8 +608,16 @@ static cudaError_t launch_direct(swe_batch *b, int n_steps, int parity0, cudaStr
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void *args[] = {(void *)&b->d_inst, (void *)&b->d_maps, (void *)&b->d_tiles, (void *)&b->ntiles,
-                    (void *)&n_steps,   (void *)&parity0,   (void *)&b->d_bar,   (void *)&b->d_err,
+    // the tile list, or the streaming variant's segments (its pass counters
+    // zeroed first)
+    if (V.kind == 1) {
+        const cudaError_t e = cudaMemsetAsync(b->d_work, 0, kWorkHead * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    void *work = V.kind == 1 ? b->d_work : static_cast<void *>(b->d_tiles);
+    int nwork = V.kind == 1 ? b->nwork : b->ntiles;
+    void *args[] = {(void *)&b->d_inst, (void *)&b->d_maps, (void *)&work,    (void *)&nwork,
+                    (void *)&n_steps,   (void *)&parity0,   (void *)&b->d_bar, (void *)&b->d_err,
                     (void *)&b->d_flags};
     return cudaLaunchKernelExC(&cfg, V.func, args);
 }
@@ -582,8 +736,9 @@ void swe_batch_destroy(swe_batch *b)
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaFree(b->pool);
     cudaFree(b->d_inst);
-    for (auto &kv : b->maps_by_box_h) cudaFree(kv.second);
+    for (auto &kv : b->maps_by_box) cudaFree(kv.second);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_work);
     cudaFree(b->d_bar);
     cudaFree(b->d_err);
     cudaFree(b->d_flags);
@@ -864,6 +1019,7 @@ swe_status swe_batch_query(swe_batch *b, int key, long long *value)
             break;
         }
         case SWE_BQ_VARIANT_COUNT: *value = (long long)variants().size(); break;
+        case SWE_BQ_KIND: *value = V.kind; break;
         default: return SWE_EINVAL;
     }
     return SWE_OK;

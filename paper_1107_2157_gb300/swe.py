@@ -24,7 +24,7 @@ SWE_KERNEL_AUTO, SWE_KERNEL_NAIVE, SWE_KERNEL_TILED, SWE_KERNEL_TEMPORAL = range
 SWE_FLAG_NONPOSITIVE, SWE_FLAG_MASS, SWE_FLAG_TIMEOUT, SWE_FLAG_FALLBACK = 1, 2, 4, 8
 (SWE_BQ_VARIANT, SWE_BQ_CTAS_PER_SM, SWE_BQ_BLOCKS, SWE_BQ_TILES, SWE_BQ_TILE_X, SWE_BQ_TILE_Y,
  SWE_BQ_STAGES, SWE_BQ_DEPTH, SWE_BQ_GRAPH, SWE_BQ_LAUNCHES, SWE_BQ_TUNED, SWE_BQ_CELLS,
- SWE_BQ_VARIANT_COUNT) = range(13)
+ SWE_BQ_VARIANT_COUNT, SWE_BQ_KIND) = range(14)
 (SWE_Q_KERNEL, SWE_Q_DEPTH, SWE_Q_PITCH, SWE_Q_LAUNCHES, SWE_Q_TILE_X, SWE_Q_TILE_Y,
  SWE_Q_STATE_PTR, SWE_Q_STEPS_PER_LAUNCH, SWE_Q_SHAPE) = range(9)
 SWE_PQ_PARTS, SWE_PQ_HALO_CELLS, SWE_PQ_LAUNCHES, SWE_PQ_ERROR = range(4)
