@@ -464,6 +464,28 @@ __global__ void __launch_bounds__(1024) cfl_final_kernel(RedGrid one, const RedG
 
 static int red_blocks(int ny) { return ny < kRedBlocks ? ny : kRedBlocks; }
 
+// Blocks of a single-grid reduction: one resident wave of ``kern`` (SMs x
+// CTAs per SM at kRedThreads threads), at most kRedBlocks and one per row.
+// A ragged second wave measured slower than a single wave with more rows per
+// block.  The results do not depend on the count: the CFL maxima are order
+// free and the mass partials are exact sums.
+template <typename K>
+static int one_wave(K kern, int ny)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 0;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRedThreads, 0) != cudaSuccess || occ < 1 ||
+        sms < 1)
+        return red_blocks(ny);
+    return std::min(red_blocks(ny), sms * occ);
+}
+
 static bool plane_vec_ok(const void *H, long long pitch, size_t es)
 {
     return ((uintptr_t)H % 16 == 0) && (((size_t)pitch * es) % 16 == 0);
@@ -486,11 +508,13 @@ cudaError_t launch_mass(int dtype, const void *H, int nx, int ny, long long pitc
 {
     RedGrid one{H, nullptr, nullptr, pitch, nx, ny, dxdy, 1.0};
     const size_t es = dtype == SWE_F64 ? 8 : 4;
-    const int B = red_blocks(ny);
+    const bool vec = plane_vec_ok(H, pitch, es);
     if (dtype == SWE_F64)
-        mass_launch<double, false>(one, nullptr, 1, B, plane_vec_ok(H, pitch, es), scratch, out_dev, s);
+        mass_launch<double, false>(one, nullptr, 1, one_wave(mass_partial_kernel<double, true, false>, ny), vec,
+                                   scratch, out_dev, s);
     else
-        mass_launch<float, false>(one, nullptr, 1, B, plane_vec_ok(H, pitch, es), scratch, out_dev, s);
+        mass_launch<float, false>(one, nullptr, 1, one_wave(mass_partial_kernel<float, true, false>, ny), vec,
+                                  scratch, out_dev, s);
     return cudaGetLastError();
 }
 
@@ -523,13 +547,15 @@ cudaError_t launch_cfl(int dtype, const void *H, const void *U, const void *V, i
                        double dx, double dy, double g, double cfl, double *scratch, double *out_dev, cudaStream_t s)
 {
     RedGrid one{H, U, V, pitch, nx, ny, dx, dy};
-    const int B = red_blocks(ny);
     if (dtype == SWE_F64)
-        cfl_launch<double, false, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+        cfl_launch<double, false, false>(one, nullptr, 1, one_wave(cfl_pass1_kernel<double, false, false>, ny), g,
+                                         cfl, scratch, out_dev, s);
     else if (plane_vec_ok(H, pitch, 4) && plane_vec_ok(U, pitch, 4) && plane_vec_ok(V, pitch, 4))
-        cfl_launch<float, true, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+        cfl_launch<float, true, false>(one, nullptr, 1, one_wave(cfl_pass1_kernel<float, true, false>, ny), g, cfl,
+                                       scratch, out_dev, s);
     else
-        cfl_launch<float, false, false>(one, nullptr, 1, B, g, cfl, scratch, out_dev, s);
+        cfl_launch<float, false, false>(one, nullptr, 1, one_wave(cfl_pass1_kernel<float, false, false>, ny), g,
+                                        cfl, scratch, out_dev, s);
     return cudaGetLastError();
 }
 

