@@ -520,9 +520,9 @@ def ensemble_record(args, steps=500):
 
 
 def fp64_record(args, peak, steps=20):
-    """The 8192x8192 grid of the default workload in FP64 (one-step kernel),
-    ``steps`` steps timed with CUDA events, against the HBM peak and the
-    measured FP64 FMA rate."""
+    """The 8192x8192 grid of the default workload in FP64 (the default FP64
+    kernel: streaming warps, two steps per launch), ``steps`` steps timed with
+    CUDA events, against the HBM peak and the measured FP64 FMA rate."""
     import numpy as np
     import torch
 
@@ -547,14 +547,18 @@ def fp64_record(args, peak, steps=20):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         status = grid.check(stream=sp)
+        per_launch = int(grid.query(swe.SWE_Q_STEPS_PER_LAUNCH))
+        kname = "lw_stream_s_kernel<double>" if int(grid.query(swe.SWE_Q_SHAPE)) in (5, 6) else \
+            ("lw_tb2_kernel<double>" if per_launch == 2 else "lw_tiled_kernel<double>")
     del h, z
     fp64_rate = swe.swe_probe_rate(swe.SWE_PROBE_FP64)
     rate = cells * steps / t
     ops = FMA_PIPE_OPS_PER_CELL_UPDATE + 3  # the three reciprocals are FP64 divisions here
+    bpu = 48 / per_launch  # the state read and written once per launch
     return {"workload": "%dx%d FP64, the default workload's initial state, %d steps" % (n, n, steps),
-            "value": rate, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
-            "hbm": {"achieved": 48 * rate / 1e9, "peak": peak, "unit": "GB/s", "frac": 48 * rate / 1e9 / peak,
-                    "algorithmic_bytes_per_cell_update": 48},
+            "value": rate, "unit": UNIT, "ms_per_step": 1e3 * t / steps, "kernel": kname,
+            "hbm": {"achieved": bpu * rate / 1e9, "peak": peak, "unit": "GB/s", "frac": bpu * rate / 1e9 / peak,
+                    "algorithmic_bytes_per_cell_update": bpu},
             "alu": {"achieved": ops * rate / 1e9, "peak": fp64_rate / 1e9, "unit": "G FP64 ops/s",
                     "frac": ops * rate / fp64_rate, "ops_per_cell_update": ops,
                     "note": "the formulas' FP64 operations, a division counted as one; the hardware spends "

@@ -53,7 +53,7 @@ typedef enum { SWE_F32 = 0, SWE_F64 = 1 } swe_dtype;
 
 /* Step kernel selection (swe_options.kernel). */
 typedef enum {
-    SWE_KERNEL_AUTO = 0,   /* FP32: TEMPORAL, FP64: TILED (the fastest measured at 8192^2) */
+    SWE_KERNEL_AUTO = 0,   /* TEMPORAL with the streaming shape (the fastest measured at 8192^2, FP32 and FP64) */
     SWE_KERNEL_NAIVE = 1,  /* one thread per cell, neighbours from global memory */
     SWE_KERNEL_TILED = 2,  /* TMA tile + halo in shared memory, one step per launch */
     SWE_KERNEL_TEMPORAL = 3, /* TMA tile + 2-cell halo, 2 steps per launch (an odd
@@ -70,13 +70,14 @@ typedef struct {
     int dtype;   /* swe_dtype; default SWE_F32 */
     int kernel;  /* swe_kernel; default SWE_KERNEL_AUTO */
     int depth;   /* 0 = default; SWE_KERNEL_TEMPORAL runs 2 steps per launch */
-    int reserved[5]; /* reserved[0]: two-step kernel shape + 1 (0 = the default: shape 5 for FP32, 4 for
+    int reserved[5]; /* reserved[0]: two-step kernel shape + 1 (0 = the default: shape 5 for FP32, 6 for
                         FP64).  Shapes 0..3 take one CTA per tile (warps x rows: 4x8, 8x4, 4x4, 8x2),
                         shape 4 is 8x4 with persistent CTAs that prefetch their next tile.  Shapes 5..8
-                        (FP32 only, SWE_EUNSUPPORTED for FP64) are warps that stream up column strips
-                        with the intermediate rows in registers and x-neighbours from warp shuffles
-                        (5: 120-column strips, two 4-row TMA chunks per warp; 6: three chunks; 7:
-                        56-column strips; 8: four 2-row chunks).  All shapes give the same bits.
+                        are warps that stream up column strips with the intermediate rows in registers
+                        and x-neighbours from warp shuffles.  FP32: 5: 120-column strips, two 4-row TMA
+                        chunks per warp; 6: three chunks; 7: 56-column strips; 8: four 2-row chunks.
+                        FP64 (5 and 6 only; SWE_EUNSUPPORTED for 7, 8): 60-column strips, registers
+                        uncapped (5) or capped for 3 CTAs per SM (6).  All shapes give the same bits.
                         Others 0 */
 } swe_options;
 

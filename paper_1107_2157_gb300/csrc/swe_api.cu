@@ -186,8 +186,8 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     if (o.kernel < SWE_KERNEL_AUTO || o.kernel > SWE_KERNEL_PACKED) return SWE_EINVAL;
     if (o.kernel == SWE_KERNEL_PACKED && o.dtype != SWE_F32) return SWE_EUNSUPPORTED;
     if (o.depth < 0 || o.depth > 2) return SWE_EUNSUPPORTED;
-    if (o.reserved[0] >= 6 && o.reserved[0] <= 9 && o.dtype != SWE_F32)
-        return SWE_EUNSUPPORTED;  // the streaming shapes are FP32
+    if (o.reserved[0] >= 8 && o.reserved[0] <= 9 && o.dtype != SWE_F32)
+        return SWE_EUNSUPPORTED;  // streaming shapes 7 and 8 are FP32 only
 
     swe_ctx *c = new (std::nothrow) swe_ctx();
     if (!c) return SWE_ENOMEM;
@@ -202,14 +202,16 @@ swe_status swe_create_ex(int nx, int ny, double dx, double dy, double dt, double
     c->esize = o.dtype == SWE_F64 ? 8 : 4;
     c->pitch = plane_pitch(nx, c->esize);
     c->plane = (size_t)c->pitch * (size_t)ny;
-    // AUTO: the fastest measured on GB300 at 8192^2.  FP32: the two-step kernel
-    // (issue-bound at 0.216 ms/step, against 0.236 for the HBM-bound one-step
-    // kernel); FP64: the one-step kernel (two steps of FP64 work per launch
-    // gain nothing at GB300's FP64 rate).
-    c->kernel = o.kernel != SWE_KERNEL_AUTO ? o.kernel : (o.dtype == SWE_F32 ? SWE_KERNEL_TEMPORAL : SWE_KERNEL_TILED);
+    // AUTO: the fastest measured on GB300 at 8192^2: the streaming two-step
+    // kernel for both.  FP32: 0.148 ms/step against 0.236 for the HBM-bound
+    // one-step kernel; FP64 (bound by GB300's FP64 rate, so the gain is the
+    // arithmetic the streaming layout does not repeat): 8.14 ms/step against
+    // 11.06.
+    c->kernel = o.kernel != SWE_KERNEL_AUTO ? o.kernel : SWE_KERNEL_TEMPORAL;
     c->depth = c->kernel == SWE_KERNEL_TEMPORAL ? 2 : 1;
-    // two-step shape: 5 (streaming warps) for FP32, 4 (persistent tiles) for FP64
-    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 9) ? o.reserved[0] - 1 : (o.dtype == SWE_F32 ? 5 : 4);
+    // two-step shape: streaming warps, 5 for FP32, 6 for FP64 (capped for 3
+    // CTAs per SM: 8.14 ms/step against 8.80 uncapped at 2)
+    c->tb_variant = (o.reserved[0] > 0 && o.reserved[0] <= 9) ? o.reserved[0] - 1 : (o.dtype == SWE_F32 ? 5 : 6);
 
     const size_t bytes = 3 * c->plane * c->esize;
     swe_status st = SWE_OK;

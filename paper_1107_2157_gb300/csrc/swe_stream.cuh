@@ -416,4 +416,294 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
     return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Scalar lanes (FP64): a lane holds VX = 16 / sizeof(T) consecutive cells
+// (one 16-byte vector per plane) as CellQ<T>; the strips, row ranges, TMA
+// ring and two-phase row loop are those of the paired lanes above.  FP64
+// runs at a small fraction of the FP32 rate on GB300, so what the streaming
+// layout saves here is arithmetic: every cell's fluxes, x-face and y-face are
+// formed once (the tiled one-step kernel forms two neighbour cells and one
+// extra face for every two cells of a row).
+// ---------------------------------------------------------------------------
+template <typename T, int LO, int NO, int CR, int NSLOT, int WARPS>
+struct StreamCfgS {
+    static constexpr int VX = 16 / (int)sizeof(T);  // cells per lane
+    static constexpr int BW = 32 * VX;              // columns a warp holds (the TMA box width)
+    static constexpr int OUT = NO * VX;             // columns it stores: lanes LO .. LO + NO - 1
+    static constexpr int ROWS = CR;
+    static constexpr uint32_t PLANE_BYTES = BW * CR * sizeof(T);
+    static constexpr uint32_t CHUNK_BYTES = 3 * PLANE_BYTES;
+    static constexpr size_t WARP_BYTES = (size_t)NSLOT * CHUNK_BYTES;
+    static constexpr size_t SMEM = WARPS * WARP_BYTES + WARPS * NSLOT * sizeof(uint64_t);
+    static_assert(LO >= 1 && LO + NO <= 31, "an overlap lane on each side of the stored ones");
+    static_assert((OUT * sizeof(T)) % 32 == 0 && (LO * VX * sizeof(T)) % 16 == 0,
+                  "32-byte output rows, 16-byte aligned boxes");
+};
+
+template <typename Cfg, int CR, int NSLOT>
+struct StreamWarpS {
+    const CUtensorMap *mH, *mU, *mV;
+    unsigned char *ring;
+    uint64_t *bars;
+    uint32_t phase;
+    int *err;
+
+    __device__ __forceinline__ void issue(int c, int x, int first)
+    {
+        const int slot = c % NSLOT;
+        unsigned char *dst = ring + (size_t)slot * Cfg::CHUNK_BYTES;
+        mbar_arrive_expect_tx(bars + slot, Cfg::CHUNK_BYTES);
+        tma_load_2d(dst, mH, bars + slot, x, first + c * CR);
+        tma_load_2d(dst + Cfg::PLANE_BYTES, mU, bars + slot, x, first + c * CR);
+        tma_load_2d(dst + 2 * Cfg::PLANE_BYTES, mV, bars + slot, x, first + c * CR);
+    }
+};
+
+// x-faces of a lane's cells: F[j] is the face left of cell j, F[VX] the face
+// right of the last cell (the upper lane's F[0]); the left neighbour of cell
+// 0 is the lower lane's last cell.  Walls are in the data (stream_ghosts_s).
+template <typename T, int VX>
+__device__ __forceinline__ void stream_xfaces_s(const CellQ<T> (&c)[VX], const Coef<T> &k, Flux3<T> (&F)[VX + 1])
+{
+    CellQ<T> L;
+    L.h = __shfl_up_sync(kFull, c[VX - 1].h, 1);
+    L.u = __shfl_up_sync(kFull, c[VX - 1].u, 1);
+    L.v = __shfl_up_sync(kFull, c[VX - 1].v, 1);
+    L.f2 = __shfl_up_sync(kFull, c[VX - 1].f2, 1);
+    L.f3 = __shfl_up_sync(kFull, c[VX - 1].f3, 1);
+    L.g3 = T(0);  // not read by an x-face
+    F[0] = xface_flux(L, c[0], k);
+#pragma unroll
+    for (int j = 1; j < VX; ++j) F[j] = xface_flux(c[j - 1], c[j], k);
+    F[VX].a = __shfl_down_sync(kFull, F[0].a, 1);
+    F[VX].b = __shfl_down_sync(kFull, F[0].b, 1);
+    F[VX].c = __shfl_down_sync(kFull, F[0].c, 1);
+}
+
+// stream_ghosts for scalar lanes: column -1 takes column 0's raw state with
+// hu negated, column nx column nx - 1's (make_cell of the mirrored state has
+// exactly the bits of mirror_x of the cell).
+template <typename T, int VX>
+__device__ __forceinline__ void stream_ghosts_s(T (&h)[VX], T (&u)[VX], T (&v)[VX], int gx0, int nx)
+{
+    const T ph = __shfl_up_sync(kFull, h[VX - 1], 1), pu = __shfl_up_sync(kFull, u[VX - 1], 1),
+            pv = __shfl_up_sync(kFull, v[VX - 1], 1);
+    const T nh = __shfl_down_sync(kFull, h[0], 1), nu = __shfl_down_sync(kFull, u[0], 1),
+            nv = __shfl_down_sync(kFull, v[0], 1);
+    T gh[VX], gu[VX], gv[VX];
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+        gh[j] = h[j];
+        gu[j] = u[j];
+        gv[j] = v[j];
+        const int col = gx0 + j;
+        if (col == -1) {
+            gh[j] = j + 1 < VX ? h[j + 1] : nh;
+            gu[j] = -(j + 1 < VX ? u[j + 1] : nu);
+            gv[j] = j + 1 < VX ? v[j + 1] : nv;
+        } else if (col == nx) {
+            gh[j] = j > 0 ? h[j - 1] : ph;
+            gu[j] = -(j > 0 ? u[j - 1] : pu);
+            gv[j] = j > 0 ? v[j - 1] : pv;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+        h[j] = gh[j];
+        u[j] = gu[j];
+        v[j] = gv[j];
+    }
+}
+
+// stream_segment for scalar lanes: two steps (ONE: one step) of output rows
+// [ya, yb) of the strip whose stored lanes start at column xs; false after a
+// timed-out wait; bad set for a stored depth that is not positive.
+template <bool EDGE, typename T, int LO, int NO, int CR, int NSLOT, int WARPS, bool ONE = false>
+__device__ __forceinline__ bool stream_segment_s(StreamWarpS<StreamCfgS<T, LO, NO, CR, NSLOT, WARPS>, CR, NSLOT> &w,
+                                                 T *__restrict__ oH, T *__restrict__ oU, T *__restrict__ oV, int nx,
+                                                 int ny, long long pitch, int xs, int ya, int yb, const Coef<T> &k,
+                                                 bool &bad)
+{
+    using C = StreamCfgS<T, LO, NO, CR, NSLOT, WARPS>;
+    constexpr int VX = C::VX;
+    using V = typename VecOf<T>::type;  // the 16-byte vector of a lane's cells
+    const int lane = threadIdx.x & 31;
+    const int bx = xs - LO * VX;
+    const int gx0 = bx + VX * lane;
+    const bool stores = lane >= LO && lane < LO + NO && gx0 < nx;
+    const int q0 = ONE ? ya : max(ya - 1, 0), q1 = ONE ? yb - 1 : min(yb, ny - 1);
+    const int first = q0 > 0 ? q0 - 1 : 0;
+    const int last = min(q1 + 1, ny - 1);
+    const int nch = (last - first) / CR + 1;
+    int issued = min(NSLOT, nch);
+    __syncwarp();
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        for (int c = 0; c < issued; ++c) w.issue(c, bx, first);
+    }
+    bool ok = true;
+    int rr = CR, ci = -1, slot = NSLOT - 1;
+    const T *rp = reinterpret_cast<const T *>(w.ring) + VX * lane;
+    using Cells = CellQ<T>[VX];
+    using Faces = Flux3<T>[VX];
+    auto next_row = [&](Cells &c) {
+        if (rr == CR) {
+            if (ok) {
+                ++ci;
+                slot = slot + 1 == NSLOT ? 0 : slot + 1;
+                if (ci >= 1 && issued < nch) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        fence_proxy_async_smem();
+                        w.issue(issued, bx, first);
+                    }
+                    ++issued;
+                }
+                if (__all_sync(kFull, mbar_wait_bounded(w.bars + slot, (w.phase >> slot) & 1u, w.err)))
+                    w.phase ^= 1u << slot;
+                else
+                    ok = false;
+                rp = reinterpret_cast<const T *>(w.ring + (size_t)slot * C::CHUNK_BYTES) + VX * lane;
+            }
+            rr = 0;
+        }
+        const T *p = rp + rr * C::BW;
+        ++rr;
+        const V h4 = *reinterpret_cast<const V *>(p);
+        const V u4 = *reinterpret_cast<const V *>(p + C::BW * CR);
+        const V v4 = *reinterpret_cast<const V *>(p + 2 * C::BW * CR);
+        T h[VX], u[VX], v[VX];
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+            h[j] = reinterpret_cast<const T *>(&h4)[j];
+            u[j] = reinterpret_cast<const T *>(&u4)[j];
+            v[j] = reinterpret_cast<const T *>(&v4)[j];
+        }
+        if (EDGE) stream_ghosts_s<T, VX>(h, u, v, gx0, nx);
+#pragma unroll
+        for (int j = 0; j < VX; ++j) c[j] = make_cell<T>(h[j], u[j], v[j], k.hg);
+    };
+    long long orow = (long long)ya * pitch + gx0;
+    auto store_next = [&](const T(&oh)[VX], const T(&ou)[VX], const T(&ov)[VX]) {
+        if (stores && ok) {
+            store_vec<T, VX>(oH + orow, oh);
+            store_vec<T, VX>(oU + orow, ou);
+            store_vec<T, VX>(oV + orow, ov);
+#pragma unroll
+            for (int j = 0; j < VX; ++j) bad |= gx0 + j < nx && !(oh[j] > T(0));
+        }
+        orow += pitch;
+    };
+    auto mirror_row = [](const Cells &c, Cells &m) {
+#pragma unroll
+        for (int j = 0; j < VX; ++j) m[j] = mirror_y(c[j]);
+    };
+    auto update = [&](const Cells &c, const Faces &d, const Faces &u, T(&oh)[VX], T(&ou)[VX], T(&ov)[VX]) {
+        Flux3<T> F[VX + 1];
+        stream_xfaces_s<T, VX>(c, k, F);
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+            oh[j] = c[j].h;
+            ou[j] = c[j].u;
+            ov[j] = c[j].v;
+            lw_update(oh[j], ou[j], ov[j], F[j], F[j + 1], d[j], u[j], k);
+        }
+    };
+    auto first_step = [&](auto top, int q, const Cells &c, Cells &n, const Faces &d, Faces &u, Cells &m) {
+        if (!decltype(top)::value || q + 1 < ny)
+            next_row(n);
+        else
+            mirror_row(c, n);
+#pragma unroll
+        for (int j = 0; j < VX; ++j) u[j] = yface_flux(c[j], n[j], k);
+        T oh[VX], ou[VX], ov[VX];
+        update(c, d, u, oh, ou, ov);
+        if (EDGE) stream_ghosts_s<T, VX>(oh, ou, ov, gx0, nx);
+#pragma unroll
+        for (int j = 0; j < VX; ++j) m[j] = make_cell<T>(oh[j], ou[j], ov[j], k.hg);
+    };
+    const std::true_type top;
+    const std::false_type inner;
+    auto second_step = [&](const Cells &c2, const Cells &n2, const Faces &d2, Faces &u2) {
+#pragma unroll
+        for (int j = 0; j < VX; ++j) u2[j] = yface_flux(c2[j], n2[j], k);
+        T oh[VX], ou[VX], ov[VX];
+        update(c2, d2, u2, oh, ou, ov);
+        store_next(oh, ou, ov);
+    };
+    auto copy = [](const Cells &a, Cells &b, const Faces &fa, Faces &fb) {
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+            b[j] = a[j];
+            fb[j] = fa[j];
+        }
+    };
+
+    Cells A1, B1, A2, B2;
+    Faces dA1, dB1, dA2, dB2;
+    if (q0 == 0) {
+        next_row(A1);
+        mirror_row(A1, B1);
+    } else {
+        next_row(B1);
+        next_row(A1);
+    }
+#pragma unroll
+    for (int j = 0; j < VX; ++j) dA1[j] = yface_flux(B1[j], A1[j], k);
+    if constexpr (ONE) {
+#pragma unroll 1
+        for (int q = ya; q < yb && ok; ++q) {
+            if (q + 1 < ny)
+                next_row(B1);
+            else
+                mirror_row(A1, B1);
+#pragma unroll
+            for (int j = 0; j < VX; ++j) dB1[j] = yface_flux(A1[j], B1[j], k);
+            T oh[VX], ou[VX], ov[VX];
+            update(A1, dA1, dB1, oh, ou, ov);
+            store_next(oh, ou, ov);
+            copy(B1, A1, dB1, dA1);
+        }
+    } else {
+        if (ya == 0) {
+            first_step(top, 0, A1, B1, dA1, dB1, A2);
+            mirror_row(A2, B2);
+            copy(B1, A1, dB1, dA1);
+        } else {
+            first_step(top, ya - 1, A1, B1, dA1, dB1, B2);
+            first_step(top, ya, B1, A1, dB1, dA1, A2);
+        }
+#pragma unroll
+        for (int j = 0; j < VX; ++j) dA2[j] = yface_flux(B2[j], A2[j], k);
+        const int qr = min(q1, ny - 2);
+        int q = ya + 1;
+#pragma unroll 1
+        for (; q + 1 <= qr && ok; q += 2) {
+            first_step(inner, q, A1, B1, dA1, dB1, B2);
+            second_step(A2, B2, dA2, dB2);
+            first_step(inner, q + 1, B1, A1, dB1, dA1, A2);
+            second_step(B2, A2, dB2, dA2);
+        }
+#pragma unroll 1
+        for (; q <= q1 && ok; ++q) {
+            first_step(top, q, A1, B1, dA1, dB1, B2);
+            second_step(A2, B2, dA2, dB2);
+            copy(B1, A1, dB1, dA1);
+            copy(B2, A2, dB2, dA2);
+        }
+        if (ok && yb == ny) {
+            mirror_row(A2, B2);
+            second_step(A2, B2, dA2, dB2);
+        }
+    }
+    if (!ok) {
+        for (int c = ci; c < issued; ++c) {
+            const int sl = c % NSLOT;
+            (void)__all_sync(kFull, mbar_wait_bounded(w.bars + sl, (w.phase >> sl) & 1u, w.err, 100000000ull));
+            w.phase ^= 1u << sl;
+        }
+    }
+    return ok;
+}
+
 }  // namespace swe

@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(NWARP * 32) lw_tb2_kernel(const __grid_constan
 // ~112 KB smem), 1: 8x4 (128x32, 256 threads), 2: 4x4 (128x16, ~61 KB),
 // 3: 8x2 (128x16, 256 threads), all with one CTA per tile; 4: 8x4 with
 // persistent CTAs (as many as fit on the device, each prefetching its next
-// tile under phase 2).  5..8 (FP32 only): warps streaming up column strips
-// (swe_stream.cu).
+// tile under phase 2).  5..8 (FP32; 5 and 6 also FP64): warps streaming up
+// column strips (swe_stream.cu).
 template <typename T, int W, int R>
 struct TbShape {
     using Cfg = Tb2Cfg<T, W, R>;
@@ -91,6 +91,10 @@ static void tb2_box_t(int *bw, int *bh)
 }
 
 bool stream_box(int variant, int *bw, int *bh);
+bool stream_box_d(int variant, int *bw, int *bh);
+cudaError_t launch_stream_d(int variant, const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
+                            long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
+                            const void *kd);
 cudaError_t launch_stream(int variant, const CUtensorMap *maps, void *out, size_t plane, int nx, int ny,
                           long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
                           const void *kd);
@@ -99,6 +103,7 @@ void tb2_box(int dtype, int variant, int *bw, int *bh)
 {
     const bool d = dtype == SWE_F64;
     if (!d && stream_box(variant, bw, bh)) return;
+    if (d && stream_box_d(variant, bw, bh)) return;
     switch (variant) {
         case 1:
         case 4: d ? tb2_box_t<double, TbShape<double, 8, 4>>(bw, bh) : tb2_box_t<float, TbShape<float, 8, 4>>(bw, bh); break;
@@ -159,8 +164,11 @@ cudaError_t launch_tb2(int dtype, int variant, const CUtensorMap *maps_in, void 
                        long long pitch, double dx, double dy, double dt, double g, int *err, cudaStream_t s,
                        const void *kd)
 {
-    if (dtype == SWE_F64)
+    if (dtype == SWE_F64) {
+        if (variant == 5 || variant == 6)
+            return launch_stream_d(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
         return launch_tb2_v<double>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
+    }
     if (variant >= 5) return launch_stream(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
     return launch_tb2_v<float>(variant, maps_in, out, plane, nx, ny, pitch, dx, dy, dt, g, err, s, kd);
 }

@@ -353,12 +353,12 @@ def test_packed_kernel_reductions_and_fp64_rejection():
     assert e.value.status == swe.SWE_EUNSUPPORTED
 
 
-def test_auto_picks_the_two_step_kernel_for_fp32_and_the_one_step_kernel_for_fp64():
+def test_auto_picks_the_streaming_two_step_kernel_for_fp32_and_fp64():
     from paper_1107_2157_gb300 import Grid, swe
-    with Grid(64, 64, 1.0, 1.0, 0.01, G, dtype="f32") as g:
-        assert g.query(swe.SWE_Q_KERNEL) == 3 and g.query(swe.SWE_Q_STEPS_PER_LAUNCH) == 2
-    with Grid(64, 64, 1.0, 1.0, 0.01, G, dtype="f64") as g:
-        assert g.query(swe.SWE_Q_KERNEL) == 2 and g.query(swe.SWE_Q_STEPS_PER_LAUNCH) == 1
+    for dtype, shape in (("f32", 5), ("f64", 6)):
+        with Grid(64, 64, 1.0, 1.0, 0.01, G, dtype=dtype) as g:
+            assert g.query(swe.SWE_Q_KERNEL) == 3 and g.query(swe.SWE_Q_STEPS_PER_LAUNCH) == 2
+            assert g.query(swe.SWE_Q_SHAPE) == shape
 
 
 @pytest.mark.parametrize("nx,ny", [(1024, 96), (517, 263)])
@@ -478,17 +478,47 @@ def test_streaming_two_step_shapes_equal_the_one_step_kernel_bitwise(variant, nx
         assert bad.size == 0, (variant, k, bad[:4], got[k][tuple(bad[0])], ref[k][tuple(bad[0])])
 
 
+STREAM64_WIDTHS = sorted({w for k in (1, 2, 3) for w in (60 * k - 2, 60 * k - 1, 60 * k, 60 * k + 1, 60 * k + 2)})
+STREAM64_CASES = [(v, nx, ny) for v in (5, 6) for nx, ny in ((701, 389), (130, 3001))] + \
+    [(v, nx, ny) for v in (5,) for nx, ny in [(1, 1), (2, 3), (5, 2), (8, 777)] +
+     [(w, 3 + w % 29) for w in STREAM64_WIDTHS]]
+
+
+@pytest.mark.parametrize("variant,nx,ny", STREAM64_CASES)
+def test_fp64_streaming_shapes_equal_the_one_step_kernel_bitwise(variant, nx, ny):
+    """FP64 streaming (two cells per lane, 60-column strips): the widths put
+    the right wall at every lane position around a strip's end; all give the
+    FP64 one-step kernel's bits after an odd number of steps."""
+    from paper_1107_2157_gb300 import Grid
+    steps = 7
+    s = si.smooth_flow_state(977 + nx, nx, ny)
+    dt = oracle.cfl_dt(s.h, s.hu, s.hv, 0.9, 1.1, G, 0.3)
+    ref = run_gpu(s, 0.9, 1.1, dt, G, steps, "f64", KERNELS["tiled"])
+    with Grid(nx, ny, 0.9, 1.1, dt, G, dtype="f64", kernel=3, variant=variant) as grid:
+        grid.set_state(*(np.ascontiguousarray(a, np.float64) for a in (s.h, s.hu, s.hv)))
+        grid.step(steps)
+        got = grid.get_state()
+        assert grid.check() == 0
+    for k in range(3):
+        bad = np.argwhere(got[k] != ref[k])
+        assert bad.size == 0, (variant, k, bad[:4])
+
+
 def test_two_step_defaults_and_fp32_only_shapes():
-    """The FP32 two-step default is streaming shape 5, the FP64 one tile
-    shape 4; the streaming shapes refuse FP64."""
+    """The two-step default is streaming shape 5 for FP32 and 6 for FP64,
+    and AUTO picks the two-step kernel for both; streaming shapes 7 and 8
+    refuse FP64."""
     from paper_1107_2157_gb300 import Grid, SweError, swe
     with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f32", kernel=3) as grid:
         assert grid.query(swe.SWE_Q_SHAPE) == 5
     with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f64", kernel=3) as grid:
-        assert grid.query(swe.SWE_Q_SHAPE) == 4
+        assert grid.query(swe.SWE_Q_SHAPE) == 6
+    for dtype in ("f32", "f64"):
+        with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype=dtype) as grid:
+            assert grid.query(swe.SWE_Q_KERNEL) == 3 and grid.query(swe.SWE_Q_STEPS_PER_LAUNCH) == 2
     with Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f32", kernel=2) as grid:
         assert grid.query(swe.SWE_Q_SHAPE) == -1
-    for v in (5, 6, 7, 8):
+    for v in (7, 8):
         with pytest.raises(SweError) as e:
             Grid(300, 200, 1.0, 1.0, 0.01, G, dtype="f64", kernel=3, variant=v)
         assert e.value.status == 6  # SWE_EUNSUPPORTED
