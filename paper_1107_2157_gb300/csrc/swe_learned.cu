@@ -64,11 +64,16 @@ struct LearnCfg {
     static constexpr int STRIP = PXB * 16;   // one 8-channel strip of a ring row, bytes
     static constexpr int X0_ROW = 2 * STRIP; // 16 channels
     static constexpr int A_ROW = 4 * STRIP;  // 32 channels
-    static constexpr int RING = 2, LW_SLOTS = 7;
+    // LW_SLOTS: group 0 writes the Lax-Wendroff row t in tick t and group 1
+    // reads it in tick t+6; group 0 reuses the slot in tick t+9, after its
+    // tick-(t+8) wait on layer 2's batch t+7, which follows group 1's whole
+    // tick t+6 (so 9 slots: group 0 does not wait on layer 3)
+    static constexpr int RING = 2, LW_SLOTS = 9;
     static constexpr int NCW = 4 * NH * NG;  // compute warps; one more issues the MMAs
     static constexpr int THREADS = (NCW + 1) * 32;
     // hidden channels per epilogue thread: group 0 (which also runs the
-    // Lax-Wendroff row and the output stage) takes C0, group 1 the rest
+    // Lax-Wendroff row) takes C0, group 1 (which also runs the output stage)
+    // the rest
     static constexpr int C0 = NG == 1 ? 32 : SWE_LEARN_C0;
     static constexpr int C1 = 32 - C0;
     static_assert(C0 % 8 == 0 && C0 >= 0 && C0 <= 32 && (NG == 2 || C0 == 32), "hidden channel split in 8-channel strips");
@@ -84,7 +89,7 @@ struct LearnCfg {
     static constexpr size_t OFF_A2 = lal16(OFF_A1 + (size_t)RING * A_ROW);
     static constexpr size_t OFF_LW = lal16(OFF_A2 + (size_t)RING * A_ROW);
     static constexpr size_t OFF_XR = OFF_LW + (size_t)LW_SLOTS * 3 * PX * 4;
-    static constexpr size_t OFF_BIAS = OFF_XR + (size_t)2 * 3 * PXB * 4;
+    static constexpr size_t OFF_BIAS = OFF_XR + (size_t)2 * 5 * PXB * 4;
     static constexpr size_t OFF_RED = lal16(OFF_BIAS + 80 * 4);
     static constexpr size_t OFF_BAR = lal16(OFF_RED + 16 * 8);
     static constexpr size_t SMEM = OFF_BAR + 128;
@@ -111,7 +116,9 @@ struct LearnArgs {
 
 // mbarriers (shared memory, in this order).  Each advances one phase per
 // batch; no barrier runs two phases ahead of a waiter, because every
-// arrival for batch t+1 follows its warp's wait on batch t.
+// arrival for batch t+1 follows its warp's wait on batch t.  B_RDY3 and B_L3
+// concern group 1 only (the output stage); group 0's part of layer 3's
+// input is published on B_RDY2, which the MMA warp waits for first.
 enum { B_RDY1 = 0, B_RDY2 = 1, B_RDY3 = 2, B_L1 = 3, B_L2 = 4, B_L3 = 5, B_FIN = 6, B_COUNT = 7 };
 
 __device__ __forceinline__ void named_bar_sync(int id, int count)
@@ -151,6 +158,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 __device__ __forceinline__ void publish(uint64_t *bar, int lane)
 {
     fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+}
+
+// The same for a hand-over of TMEM writes only (no shared-memory operand
+// was written): no proxy fence.
+__device__ __forceinline__ void publish_tmem(uint64_t *bar, int lane)
+{
     tc::fence_before_sync();
     __syncwarp();
     if (lane == 0) mbar_arrive(bar);
@@ -291,7 +307,7 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
     if (tid == 0) {
         mbar_init(bars + B_RDY1, C::NCW);
         mbar_init(bars + B_RDY2, C::NCW);
-        mbar_init(bars + B_RDY3, C::NCW);
+        mbar_init(bars + B_RDY3, C::NCW - C::PX / 32);  // group 1: the output stage
         mbar_init(bars + B_L1, 1);
         mbar_init(bars + B_L2, 1);
         mbar_init(bars + B_L3, 1);
@@ -402,8 +418,8 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
         // ------------------------------------------------------------------
         // Compute warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31: pixel
         // px = 128 hh + 32 q + lane of half hh, channel group g.  Group 0
-        // (PX threads, one per pixel) also runs the Lax-Wendroff step and
-        // the output stage.
+        // (PX threads, one per pixel) also runs the Lax-Wendroff step, group
+        // 1 the output stage and the mass sums.
         // ------------------------------------------------------------------
         const int q = warp & 3, hh = (warp >> 2) % NH, g = warp / (4 * NH);
         const int px = 128 * hh + 32 * q + lane;
@@ -476,32 +492,46 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                 for (int b = 0; b < 3; ++b) {
                     arm_hidden(t1 + b * 32, sBias + ch);
                     arm_hidden(t2 + b * 32, sBias + 32 + ch);
-                    if (lw_thread) arm<16>(t3 + b * 16, sBias + 64);
+                    if (!lw_thread) {
+                        tc::st_x4_async(t3 + b * 16, sBias + 64);
+                        tc::wait_st();
+                    }
                 }
                 double hs = 0.0;
-                int lws = 0;  // lw ring slot of row t (t mod 7)
+                int lws = 0;  // lw ring slot of row t (t mod 9)
 #pragma unroll 1
                 for (int t = 0; t < T; ++t, lws = lws == C::LW_SLOTS - 1 ? 0 : lws + 1) {
                     const uint32_t parW = (nb + (uint32_t)t - 1u) & 1u;  // batch t-1
                     const bool publish_t = t + 1 < T;
                     // ---- Lax-Wendroff row t; network input x0[t] ----
                     if (lw_thread && t < H) {
-                        float *xr = sXR + (t & 1) * 3 * C::PXB;
+                        // the row's cells (state and x-fluxes) for the
+                        // neighbours' x-faces
+                        float *xr = sXR + (t & 1) * 5 * C::PXB;
                         if (inside) {
                             xr[px + 1] = cur.h;
                             xr[C::PXB + px + 1] = cur.u;
                             xr[2 * C::PXB + px + 1] = cur.v;
+                            xr[3 * C::PXB + px + 1] = cur.f2;
+                            xr[4 * C::PXB + px + 1] = cur.f3;
                         }
                         named_bar_sync(1, C::PX);
                         uint4 x8 = zero4();
                         if (inside) {
-                            const CellQ<float> left =
-                                px == 0 ? mirror_x(cur)
-                                        : make_cell<float>(xr[px], xr[C::PXB + px], xr[2 * C::PXB + px], kc.hg);
-                            const CellQ<float> right =
-                                px == W - 1
-                                    ? mirror_x(cur)
-                                    : make_cell<float>(xr[px + 2], xr[C::PXB + px + 2], xr[2 * C::PXB + px + 2], kc.hg);
+                            // a neighbour's h, hu, hv, f2, f3 as its own thread
+                            // formed them (g3 is not read by an x-face)
+                            auto xcell = [&](int i) {
+                                CellQ<float> c;
+                                c.h = xr[i];
+                                c.u = xr[C::PXB + i];
+                                c.v = xr[2 * C::PXB + i];
+                                c.f2 = xr[3 * C::PXB + i];
+                                c.f3 = xr[4 * C::PXB + i];
+                                c.g3 = 0.0f;
+                                return c;
+                            };
+                            const CellQ<float> left = px == 0 ? mirror_x(cur) : xcell(px);
+                            const CellQ<float> right = px == W - 1 ? mirror_x(cur) : xcell(px + 2);
                             const CellQ<float> up = t + 1 < H ? nxt : mirror_y(cur);
                             const Flux3<float> Fl = xface_flux(left, cur, kc);
                             const Flux3<float> Fr = xface_flux(cur, right, kc);
@@ -547,15 +577,21 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                         epilogue(t2 + mod3(r2) * 32, sBias + 32 + ch, sA2 + (r2 & 1) * C::A_ROW + sw, inside);
                     if (publish_t) publish(bars + B_RDY2, lane);
                     // ---- E3: corrected row t-6 ----
-                    if (t >= 1) wait(bars + B_L3, parW);
+                    if (!lw_thread && t >= 1) wait(bars + B_L3, parW);
                     const int r3 = t - 6;
-                    if (lw_thread && r3 >= 0 && r3 < H) {
+                    if (!lw_thread && r3 >= 0 && r3 < H) {
+                        // only columns 0..2 of a layer-3 block are outputs
+                        // (the padding columns are never read): four
+                        // columns are read and re-armed
                         const uint32_t ta = t3 + mod3(r3) * 16;
-                        float v[16];
-                        tmem_load<16>(ta, v);
-                        arm<16>(ta, sBias + 64);
+                        uint32_t v4[4];
+                        tc::ld_x4_async(ta, v4);
+                        tc::wait_ld(v4);
+                        tc::st_x4_async(ta, sBias + 64);
+                        const float v[3] = {__uint_as_float(v4[0]), __uint_as_float(v4[1]), __uint_as_float(v4[2])};
+                        tc::wait_st();
                         if (inside) {
-                            const int s3 = lws >= 6 ? lws - 6 : lws + 1;  // (t - 6) mod 7
+                            const int s3 = lws >= 6 ? lws - 6 : lws + 3;  // (t - 6) mod 9
                             const float *lw = sLW + s3 * 3 * C::PX;
                             const long long o = (long long)r3 * pitch + px;
                             dst[o] = __fmaf_rn(v[0], a.os_h, lw[px]);
@@ -564,16 +600,21 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                             hs += (double)(v[0] * a.os_h);
                         }
                     }
-                    if (publish_t) publish(bars + B_RDY3, lane);
+                    if (!lw_thread && publish_t) publish_tmem(bars + B_RDY3, lane);
                 }
                 nb += (uint32_t)(T - 1);
                 // ---- mass projection: the mean h correction becomes the pending offset ----
-                if (lw_thread) {
+                // (group 1 holds the sums and wrote the corrected rows; the
+                // barrier also orders those writes before group 0 reads
+                // them as the next step's input)
+                if (!lw_thread) {
                     double s = hs;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) sRed[warp] = s;
-                    named_bar_sync(1, C::PX);
+                    if (lane == 0) sRed[warp - 4 * NH] = s;
+                }
+                named_bar_sync(2, C::NCW * 32);
+                if (lw_thread) {
                     double tot = 0.0;
                     for (int w = 0; w < 4 * NH; ++w) tot += sRed[w];
                     m = a.project ? (float)(tot / ((double)W * (double)H)) : 0.0f;

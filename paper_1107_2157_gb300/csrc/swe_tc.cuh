@@ -169,6 +169,13 @@ __device__ __forceinline__ void ld_x8_async(uint32_t taddr, uint32_t (&r)[8])
                  : "r"(taddr)
                  : "memory");
 }
+__device__ __forceinline__ void ld_x4_async(uint32_t taddr, uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
 // One wait for every load issued so far by the warp; the arrays passed are
 // the destinations whose values it releases.
 __device__ __forceinline__ void wait_ld(uint32_t (&a)[16])
@@ -187,6 +194,13 @@ __device__ __forceinline__ void wait_ld(uint32_t (&a)[8], uint32_t (&b)[16])
                    "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
                    "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]),
                    "+r"(b[15])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void wait_ld(uint32_t (&a)[4])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
                  :
                  : "memory");
 }
@@ -219,6 +233,13 @@ __device__ __forceinline__ void st_x8_async(uint32_t taddr, const float *v)
                  "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
                  "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
                  "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void st_x4_async(uint32_t taddr, const float *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3]))
                  : "memory");
 }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
