@@ -400,6 +400,21 @@ def run_ours(args):
         barrier()
         e2e_runs.append(f0.elapsed_time(f1) / 1e3)
     t_e2e = statistics.median(e2e_runs)
+    # the two state copies of a job, timed alone (the job's floor on this
+    # machine's host link): H2D of the three planes, D2H of the three planes
+    link = {}
+    for name, fn in (("h2d", lambda: grid.set_state(h_host, z_host, z_host, stream=sp)),
+                     ("d2h", lambda: grid.get_state(out=out_host, stream=sp, sync=False))):
+        runs = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            fn()
+            f1.record(stream)
+            torch.cuda.synchronize()
+            runs.append(f0.elapsed_time(f1) / 1e3)
+        link[name] = statistics.median(runs)
 
     # max over ranks
     t_job, t_steps, t_e2e = aggregate_over_ranks([t_job, t_steps, t_e2e], ws, device="cuda")
@@ -454,10 +469,13 @@ def run_ours(args):
         "e2e": {"value": whole_job_rate(ws, cells, args.steps, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * 4 * cells / args.steps, "d2h_bytes_per_step": 3 * 4 * cells / args.steps,
                 "job_s": [round(t, 6) for t in e2e_runs],
+                "h2d_s": round(link["h2d"], 6), "d2h_s": round(link["d2h"], 6),
+                "h2d_gbs": 3 * 4 * cells / link["h2d"] / 1e9, "d2h_gbs": 3 * 4 * cells / link["d2h"] / 1e9,
                 "note": "the job through the C ABI from pinned host buffers: host->device state (3 x FP32 "
                         "planes), FP64 CFL dt, K steps, FP64 mass, device->host state; the state crosses "
                         "once per K-step job, so the bytes per step are the plane bytes / K; median of "
-                        "three jobs (job_s)"},
+                        "three jobs (job_s); h2d_s / d2h_s: the two copies timed alone, the floor the host "
+                        "link puts under every job"},
         "gpu_launches": int(launches) + 7,  # + CFL (4 launches) + coefficients (1) + mass (2)
         "clocks": clocks,
         "cpu_baseline": cpu,

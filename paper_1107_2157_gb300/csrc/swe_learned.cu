@@ -34,9 +34,11 @@
 // Mass projection: the mean of the h correction over the instance is known
 // only when the sweep ends, so it is kept as a pending offset m: the state
 // written by a sweep is (true h) + m, the next sweep subtracts m as it
-// loads, and after the last step every h is corrected in place.  The
-// arithmetic is the same as the unfused path's (correct, then subtract the
-// mean).
+// loads, and after the last step every h is corrected in place.  The steps
+// are the unfused path's (correct, then subtract the mean); the sum behind
+// the mean is taken per pixel in FP32 over blocks of 16 rows and in FP64
+// across blocks and pixels (the unfused path sums in FP64 throughout), so
+// the two means agree to FP32 rounding of 16-term sums.
 #include <algorithm>
 #include <mutex>
 
@@ -190,8 +192,9 @@ __device__ __forceinline__ void load16(const float *p, float (&b)[16])
 // Arms CPT accumulator columns at taddr with the bias (TMEM store); an odd
 // 8 columns first, so that every 16-column store starts on a multiple of 16
 // when taddr's column is a multiple of 16 or sits 8 past one.
-// The stores are issued back to back and waited for once.
-template <int CPT>
+// The stores are issued back to back and waited for once (WAIT), or the
+// caller waits (tc::wait_st) before the columns are handed to the MMAs.
+template <int CPT, bool WAIT = true>
 __device__ __forceinline__ void arm(uint32_t taddr, const float *bias)
 {
     static_assert(CPT % 8 == 0, "8-column granules");
@@ -207,7 +210,7 @@ __device__ __forceinline__ void arm(uint32_t taddr, const float *bias)
         load16(bias + LEAD + 16 * c, b);
         tc::st_x16_async(taddr + LEAD + 16 * c, b);
     }
-    tc::wait_st();
+    if constexpr (WAIT) tc::wait_st();
 }
 
 // CPT (8, 16 or 24) accumulator columns at taddr into v, in the same
@@ -250,7 +253,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bia
 {
     float v[CPT];
     tmem_load<CPT>(taddr, v);
-    arm<CPT>(taddr, bias);
+    arm<CPT, false>(taddr, bias);  // completes under the activations
 #pragma unroll
     for (int c = 0; c < CPT / 8; ++c) {
         float y[8];
@@ -260,6 +263,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bia
                                    pack_bf16x2(y[6], y[7]));
         *reinterpret_cast<uint4 *>(dst + c * strip) = valid ? o : zero4();
     }
+    tc::wait_st();
 }
 
 // Copies the per-tap B images of one layer (global; block (tap, s) is
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
         uint32_t nb = 0;  // batches of the finished sweeps
         // waits for ``bar`` (per thread); records a give-up for everyone
         auto wait = [&](uint64_t *bar, uint32_t par) {
-            if (!*sAbort && !mbar_wait_bounded(bar, par, a.err)) *sAbort = 1;
+            if (!mbar_try_wait(bar, par) && !*sAbort && !mbar_wait_bounded(bar, par, a.err)) *sAbort = 1;
             __syncwarp();
             tc::fence_after_sync();
         };
@@ -497,7 +501,8 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                         tc::wait_st();
                     }
                 }
-                double hs = 0.0;
+                double hs = 0.0;  // this pixel's h corrections: FP32 sums of 16 rows, added in FP64
+                float hs16 = 0.0f;
                 int lws = 0;  // lw ring slot of row t (t mod 9)
 #pragma unroll 1
                 for (int t = 0; t < T; ++t, lws = lws == C::LW_SLOTS - 1 ? 0 : lws + 1) {
@@ -589,7 +594,6 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                         tc::wait_ld(v4);
                         tc::st_x4_async(ta, sBias + 64);
                         const float v[3] = {__uint_as_float(v4[0]), __uint_as_float(v4[1]), __uint_as_float(v4[2])};
-                        tc::wait_st();
                         if (inside) {
                             const int s3 = lws >= 6 ? lws - 6 : lws + 3;  // (t - 6) mod 9
                             const float *lw = sLW + s3 * 3 * C::PX;
@@ -597,8 +601,13 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                             dst[o] = __fmaf_rn(v[0], a.os_h, lw[px]);
                             dst[o + plane] = __fmaf_rn(v[1], a.os_u, lw[C::PX + px]);
                             dst[o + 2 * plane] = __fmaf_rn(v[2], a.os_u, lw[2 * C::PX + px]);
-                            hs += (double)(v[0] * a.os_h);
+                            hs16 += v[0] * a.os_h;
                         }
+                        if ((r3 & 15) == 15 || r3 == H - 1) {
+                            hs += (double)hs16;
+                            hs16 = 0.0f;
+                        }
+                        tc::wait_st();
                     }
                     if (!lw_thread && publish_t) publish_tmem(bars + B_RDY3, lane);
                 }
