@@ -395,14 +395,24 @@ __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)
 // A product that a later add or subtract may not absorb.  Unlike the scalar
 // mul.rn, a packed mul.rn.f32x2 whose result feeds an add/sub.rn.f32x2 is
 // fused into one FMA by the compiler (measured on sm_103a, --fmad=false or
-// not), which changes the rounding; two scalar __fmul_rn are not.  Every
-// product that feeds a sum goes through this.
+// not), which changes the rounding; two scalar __fmul_rn are not.
 __device__ __forceinline__ F2 mul2_rn(F2 a, F2 b)
 {
     float a0, a1, b0, b1;
     unpack2(a, a0, a1);
     unpack2(b, b0, b1);
     return pack2(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
+}
+// The same product in one packed instruction: the FMA a*b + nz with nz =
+// (-0, -0).  RN(a*b + (-0)) = RN(a*b) for every a, b (a zero product keeps
+// its sign: +0 + -0 = +0, -0 + -0 = -0), and an FMA is not absorbed into a
+// later add.  nz must be a run-time value: given the constant -0 the
+// compiler turns the FMA back into a multiply, and fuses that (measured).
+__device__ __forceinline__ F2 mul2_nf(F2 a, F2 b, F2 nz)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(nz.v));
+    return r;
 }
 __device__ __forceinline__ F2 rcp2(F2 x)
 {
@@ -424,14 +434,16 @@ struct CellQ2 {
 struct Flux2 {
     F2 a, b, c;
 };
-// the coefficients broadcast to both lanes
+// the coefficients broadcast to both lanes; nz = (-0, -0) for mul2_nf,
+// formed at run time as -0 * g/2 (g > 0 is checked when a grid is created)
 struct Coef2 {
-    F2 hx, hy, lx, ly, hg, qg;
+    F2 hx, hy, lx, ly, hg, qg, nz;
 };
 __device__ __forceinline__ Coef2 coef2(const Coef<float> &k)
 {
+    const float z = __fmul_rn(-0.0f, k.hg);
     return {pack2(k.hx, k.hx), pack2(k.hy, k.hy), pack2(k.lx, k.lx), pack2(k.ly, k.ly), pack2(k.hg, k.hg),
-            pack2(k.qg, k.qg)};
+            pack2(k.qg, k.qg), pack2(z, z)};
 }
 
 // make_cell on two cells
@@ -446,7 +458,7 @@ __device__ __forceinline__ CellQ2 make_cell2(F2 h, F2 u, F2 v, const Coef2 &k)
     const F2 uu = mul2(u, inv);
     const F2 vv = mul2(v, inv);
     c.f2 = fma2(u, uu, p);
-    c.f3 = mul2_rn(u, vv);  // differenced by the face steps
+    c.f3 = mul2_nf(u, vv, k.nz);  // differenced by the face steps
     c.g3 = fma2(v, vv, p);
     return c;
 }
@@ -485,7 +497,7 @@ __device__ __forceinline__ Flux2 xface_flux2(const CellQ2 &L, const CellQ2 &R, c
     Flux2 F;
     F.a = Uf;
     F.b = fma2(Uf, uf, mul2(mul2(k.qg, Hf), Hf));
-    F.c = mul2_rn(Vf, uf);  // differenced by the update
+    F.c = mul2_nf(Vf, uf, k.nz);  // differenced by the update
     return F;
 }
 
@@ -499,7 +511,7 @@ __device__ __forceinline__ Flux2 yface_flux2(const CellQ2 &D, const CellQ2 &U, c
     const F2 vf = mul2(Vf, inv);
     Flux2 G;
     G.a = Vf;
-    G.b = mul2_rn(Uf, vf);  // differenced by the update
+    G.b = mul2_nf(Uf, vf, k.nz);  // differenced by the update
     G.c = fma2(Vf, vf, mul2(mul2(k.qg, Hf), Hf));
     return G;
 }
