@@ -295,13 +295,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
             // of the row loop instead of two cuts instruction-fetch stalls
             // and spills and measured 18 % faster (0.468 against 0.568 ms per
             // step on the 512-grid ensemble at 3 CTAs/SM).
+            // The cells are paired (c_0, c_2), (c_1, c_3) in each lane: the
+            // x-face pairs then line up without regrouping, and this kernel
+            // (one copy of the row loop, more live state than the
+            // single-grid one) measured 3 % faster so; the single-grid
+            // kernel keeps (c_0, c_1), (c_2, c_3), which its compiled code
+            // favours.  Either pairing gives the same bits.
             bool bad = false;
             float *oh = o, *ou = o + plane, *ov = o + 2 * plane;
             if (two)
-                ok = stream_segment<true>(w, oh, ou, ov, nx, ny, pitch, xs, r.ya, r.yb, k2, bad);
+                ok = stream_segment<true, VP, LO, NO, CR, NSLOT, WARPS, false, true>(w, oh, ou, ov, nx, ny, pitch, xs,
+                                                                                     r.ya, r.yb, k2, bad);
             else  // the one-step pass: an odd count's last
-                ok = stream_segment<true, VP, LO, NO, CR, NSLOT, WARPS, true>(w, oh, ou, ov, nx, ny, pitch, xs, r.ya,
-                                                                              r.yb, k2, bad);
+                ok = stream_segment<true, VP, LO, NO, CR, NSLOT, WARPS, true, true>(w, oh, ou, ov, nx, ny, pitch, xs,
+                                                                                    r.ya, r.yb, k2, bad);
             if (__any_sync(kFull, bad) && lane == 0) atomicOr(&flags[r.inst], SWE_FLAG_NONPOSITIVE);
         }
         // every warp reaches the barrier, also after a timed-out wait

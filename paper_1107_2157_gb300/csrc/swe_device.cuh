@@ -339,7 +339,7 @@ __device__ __forceinline__ void lw_update(T &h, T &u, T &v, const Flux3<T> &Fl, 
 // exactly the IEEE operation the scalar functions above perform, and the
 // reciprocal is taken per lane with the same instruction, so every lane of
 // a paired result has the bits of the scalar computation, provided no packed
-// product feeds a packed add or subtract (see mul2_rn).  Used by the tile
+// product feeds a packed add or subtract (see mul2_nf).  Used by the tile
 // routine for cells away from an x-wall.
 // ---------------------------------------------------------------------------
 struct F2 {
@@ -395,16 +395,8 @@ __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c)
 // A product that a later add or subtract may not absorb.  Unlike the scalar
 // mul.rn, a packed mul.rn.f32x2 whose result feeds an add/sub.rn.f32x2 is
 // fused into one FMA by the compiler (measured on sm_103a, --fmad=false or
-// not), which changes the rounding; two scalar __fmul_rn are not.
-__device__ __forceinline__ F2 mul2_rn(F2 a, F2 b)
-{
-    float a0, a1, b0, b1;
-    unpack2(a, a0, a1);
-    unpack2(b, b0, b1);
-    return pack2(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
-}
-// The same product in one packed instruction: the FMA a*b + nz with nz =
-// (-0, -0).  RN(a*b + (-0)) = RN(a*b) for every a, b (a zero product keeps
+// not), which changes the rounding.  So the product is taken as the packed
+// FMA a*b + nz with nz = (-0, -0).  RN(a*b + (-0)) = RN(a*b) for every a, b (a zero product keeps
 // its sign: +0 + -0 = +0, -0 + -0 = -0), and an FMA is not absorbed into a
 // later add.  nz must be a run-time value: given the constant -0 the
 // compiler turns the FMA back into a multiply, and fuses that (measured).

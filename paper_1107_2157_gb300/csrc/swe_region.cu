@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(S::NT) region_lw_kernel(const __grid_constant_
     const Window<T, int> oH{out.h + o, CX, CY, op, vx, vy};
     const Window<T, int> oU{out.u + o, CX, CY, op, vx, vy};
     const Window<T, int> oV{out.v + o, CX, CY, op, vx, vy};
-    CtaRun<S::NT> run{err};
+    // (-0, -0) for the packed products, as -0 * g (g > 0 is checked on the
+    // host): a run-time value, which the compiler cannot fold into a multiply
+    const float nz0 = __fmul_rn(-0.0f, (float)k.g);
+    CtaRun<S::NT> run{err, pack2(nz0, nz0)};
     if constexpr (BED) {
         const auto B = array<int>(sB, CX, CY, S::BX);
         const auto Hx = array<int>(hxy, S::TX + 1, S::TY, S::TX + 1);

@@ -3,10 +3,12 @@
 // single-grid kernel (swe_stream.cu) and the batched one (swe_batch.cu).
 //
 // A warp owns a strip of OUT grid columns starting at xs and a range of its
-// rows.  Each lane holds VX = 2 VP consecutive columns (VP cell pairs on the
-// packed f32x2 pipe); lanes LO .. LO + NO - 1 hold the strip, lane LO - 1
-// and lane LO + NO the columns just outside it.  (The default shape: VP = 2,
-// lane l holds xs - 4 + 4l .. xs - 1 + 4l, lanes 1..30 store 120 columns.)
+// rows.  Each lane holds VX = 2 VP consecutive columns c_0 .. c_{VX-1} as VP
+// cell pairs on the packed f32x2 pipe, pair p = (c_{2p}, c_{2p+1}), or with
+// SPLIT pair p = (c_p, c_{p+VP}) (the same for VP = 1); lanes LO .. LO + NO
+// - 1 hold the strip, lane LO - 1 and lane LO + NO the columns just outside
+// it.  (The default shape: VP = 2, lane l holds xs - 4 + 4l .. xs - 1 + 4l,
+// lanes 1..30 store 120 columns.)
 // For each row q the warp takes the first step of row q (the intermediate
 // state, from input rows q-1..q+1) and then the second step of row q-1 (from
 // intermediate rows q-2..q).  The intermediate rows never leave registers:
@@ -62,7 +64,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Fr[p] = (c_{2p}|c_{2p+1}, c_{2p+1}|c_{2p+2}), where c_{-1} is the lower
 // lane's last cell and the face right of the last cell is the upper lane's
 // first face.  Walls are in the data (stream_ghosts).
-template <int VP>
+template <int VP, bool SPLIT = false>
 __device__ __forceinline__ void stream_xfaces(const CellQ2 (&c)[VP], const Coef2 &k2, Flux2 (&Fl)[VP],
                                               Flux2 (&Fr)[VP])
 {
@@ -73,17 +75,33 @@ __device__ __forceinline__ void stream_xfaces(const CellQ2 (&c)[VP], const Coef2
     L.f2 = __shfl_up_sync(kFull, hi2(c[VP - 1].f2), 1);
     L.f3 = __shfl_up_sync(kFull, hi2(c[VP - 1].f3), 1);
     L.g3 = 0.0f;  // not read by an x-face
-    Fl[0] = xface_flux2(pair_cells(L, cell_lo(c[0])), c[0], k2);
+    if constexpr (SPLIT) {
+        // pair p = (c_p, c_{p+VP}): the left cells of pair p >= 1 are pair
+        // p - 1, those of pair 0 are (c_{-1}, c_{VP-1}); Fr[p] = Fl[p+1], and
+        // the last pair's right faces are (c_VP's left face, the upper
+        // lane's first face)
+        Fl[0] = xface_flux2(pair_cells(L, cell_lo(c[VP - 1])), c[0], k2);
 #pragma unroll
-    for (int p = 1; p < VP; ++p) Fl[p] = xface_flux2(pair_cells(cell_hi(c[p - 1]), cell_lo(c[p])), c[p], k2);
-    const float fa = __shfl_down_sync(kFull, lo2(Fl[0].a), 1);
-    const float fb = __shfl_down_sync(kFull, lo2(Fl[0].b), 1);
-    const float fc = __shfl_down_sync(kFull, lo2(Fl[0].c), 1);
+        for (int p = 1; p < VP; ++p) Fl[p] = xface_flux2(c[p - 1], c[p], k2);
+        const float fa = __shfl_down_sync(kFull, lo2(Fl[0].a), 1);
+        const float fb = __shfl_down_sync(kFull, lo2(Fl[0].b), 1);
+        const float fc = __shfl_down_sync(kFull, lo2(Fl[0].c), 1);
 #pragma unroll
-    for (int p = 0; p + 1 < VP; ++p)
-        Fr[p] = flux_pair(hi2(Fl[p].a), hi2(Fl[p].b), hi2(Fl[p].c), lo2(Fl[p + 1].a), lo2(Fl[p + 1].b),
-                          lo2(Fl[p + 1].c));
-    Fr[VP - 1] = flux_pair(hi2(Fl[VP - 1].a), hi2(Fl[VP - 1].b), hi2(Fl[VP - 1].c), fa, fb, fc);
+        for (int p = 0; p + 1 < VP; ++p) Fr[p] = Fl[p + 1];
+        Fr[VP - 1] = flux_pair(hi2(Fl[0].a), hi2(Fl[0].b), hi2(Fl[0].c), fa, fb, fc);
+    } else {
+        Fl[0] = xface_flux2(pair_cells(L, cell_lo(c[0])), c[0], k2);
+#pragma unroll
+        for (int p = 1; p < VP; ++p) Fl[p] = xface_flux2(pair_cells(cell_hi(c[p - 1]), cell_lo(c[p])), c[p], k2);
+        const float fa = __shfl_down_sync(kFull, lo2(Fl[0].a), 1);
+        const float fb = __shfl_down_sync(kFull, lo2(Fl[0].b), 1);
+        const float fc = __shfl_down_sync(kFull, lo2(Fl[0].c), 1);
+#pragma unroll
+        for (int p = 0; p + 1 < VP; ++p)
+            Fr[p] = flux_pair(hi2(Fl[p].a), hi2(Fl[p].b), hi2(Fl[p].c), lo2(Fl[p + 1].a), lo2(Fl[p + 1].b),
+                              lo2(Fl[p + 1].c));
+        Fr[VP - 1] = flux_pair(hi2(Fl[VP - 1].a), hi2(Fl[VP - 1].b), hi2(Fl[VP - 1].c), fa, fb, fc);
+    }
 }
 
 // Reflective walls as ghost columns: in a strip that reaches a wall, the
@@ -93,16 +111,17 @@ __device__ __forceinline__ void stream_xfaces(const CellQ2 (&c)[VP], const Coef2
 // of make_cell(h, hu, hv) (every product involving hu changes sign and
 // nothing else), so the faces next to a wall are those of the other
 // kernels.  gx0 is the grid column of the lane's first cell.
-template <int VP>
+template <int VP, bool SPLIT = false>
 __device__ __forceinline__ void stream_ghosts(F2 (&h)[VP], F2 (&u)[VP], F2 (&v)[VP], int gx0, int nx)
 {
     constexpr int VX = 2 * VP;
     float hs[VX], us[VX], vs[VX];
 #pragma unroll
     for (int p = 0; p < VP; ++p) {
-        unpack2(h[p], hs[2 * p], hs[2 * p + 1]);
-        unpack2(u[p], us[2 * p], us[2 * p + 1]);
-        unpack2(v[p], vs[2 * p], vs[2 * p + 1]);
+        const int j0 = SPLIT ? p : 2 * p, j1 = SPLIT ? p + VP : 2 * p + 1;  // the pair's columns
+        unpack2(h[p], hs[j0], hs[j1]);
+        unpack2(u[p], us[j0], us[j1]);
+        unpack2(v[p], vs[j0], vs[j1]);
     }
     // the lower lane's last cell and the upper lane's first cell
     const float ph = __shfl_up_sync(kFull, hs[VX - 1], 1), pu = __shfl_up_sync(kFull, us[VX - 1], 1),
@@ -128,20 +147,21 @@ __device__ __forceinline__ void stream_ghosts(F2 (&h)[VP], F2 (&u)[VP], F2 (&v)[
     }
 #pragma unroll
     for (int p = 0; p < VP; ++p) {
-        h[p] = pack2(gh[2 * p], gh[2 * p + 1]);
-        u[p] = pack2(gu[2 * p], gu[2 * p + 1]);
-        v[p] = pack2(gv[2 * p], gv[2 * p + 1]);
+        const int j0 = SPLIT ? p : 2 * p, j1 = SPLIT ? p + VP : 2 * p + 1;
+        h[p] = pack2(gh[j0], gh[j1]);
+        u[p] = pack2(gu[j0], gu[j1]);
+        v[p] = pack2(gv[j0], gv[j1]);
     }
 }
 
 // One step of a row of a lane's cells ``c`` (pairs), given the y-face fluxes
 // below (gd) and above (gu); returns the updated (h, hu, hv) pairs.
-template <int VP>
+template <int VP, bool SPLIT = false>
 __device__ __forceinline__ void stream_update(const CellQ2 (&c)[VP], const Flux2 (&gd)[VP], const Flux2 (&gu)[VP],
                                               const Coef2 &k2, F2 (&oh)[VP], F2 (&ou)[VP], F2 (&ov)[VP])
 {
     Flux2 Fl[VP], Fr[VP];
-    stream_xfaces<VP>(c, k2, Fl, Fr);
+    stream_xfaces<VP, SPLIT>(c, k2, Fl, Fr);
 #pragma unroll
     for (int p = 0; p < VP; ++p) {
         oh[p] = c[p].h;
@@ -171,13 +191,18 @@ struct StreamWarp {
     }
 };
 
-template <int VP>
+template <int VP, bool SPLIT = false>
 __device__ __forceinline__ void store_cells(float *dst, const F2 (&x)[VP])
 {
     if constexpr (VP == 2) {
         float4 t;
-        unpack2(x[0], t.x, t.y);
-        unpack2(x[1], t.z, t.w);
+        if constexpr (SPLIT) {  // pairs (c_0, c_2), (c_1, c_3)
+            unpack2(x[0], t.x, t.z);
+            unpack2(x[1], t.y, t.w);
+        } else {
+            unpack2(x[0], t.x, t.y);
+            unpack2(x[1], t.z, t.w);
+        }
         *reinterpret_cast<float4 *>(dst) = t;
     } else {
         float2 t;
@@ -195,7 +220,7 @@ __device__ __forceinline__ void store_cells(float *dst, const F2 (&x)[VP])
 // swapped between the halves (the cells and faces of the current row are
 // the "next" ones of the row before), so nothing is copied from row to row;
 // input rows and output rows are walked with running offsets.
-template <bool EDGE, int VP, int LO, int NO, int CR, int NSLOT, int WARPS, bool ONE = false>
+template <bool EDGE, int VP, int LO, int NO, int CR, int NSLOT, int WARPS, bool ONE = false, bool SPLIT = false>
 __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT, WARPS> &w, float *__restrict__ oH,
                                                float *__restrict__ oU, float *__restrict__ oV, int nx, int ny,
                                                long long pitch, int xs, int ya, int yb, const Coef2 &k2,
@@ -257,12 +282,21 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
             const float4 h4 = *reinterpret_cast<const float4 *>(p);
             const float4 u4 = *reinterpret_cast<const float4 *>(p + C::BW * CR);
             const float4 v4 = *reinterpret_cast<const float4 *>(p + 2 * C::BW * CR);
-            h[0] = pack2(h4.x, h4.y);
-            h[VP - 1] = pack2(h4.z, h4.w);
-            u[0] = pack2(u4.x, u4.y);
-            u[VP - 1] = pack2(u4.z, u4.w);
-            v[0] = pack2(v4.x, v4.y);
-            v[VP - 1] = pack2(v4.z, v4.w);
+            if constexpr (SPLIT) {  // pairs (c_0, c_2), (c_1, c_3)
+                h[0] = pack2(h4.x, h4.z);
+                h[VP - 1] = pack2(h4.y, h4.w);
+                u[0] = pack2(u4.x, u4.z);
+                u[VP - 1] = pack2(u4.y, u4.w);
+                v[0] = pack2(v4.x, v4.z);
+                v[VP - 1] = pack2(v4.y, v4.w);
+            } else {
+                h[0] = pack2(h4.x, h4.y);
+                h[VP - 1] = pack2(h4.z, h4.w);
+                u[0] = pack2(u4.x, u4.y);
+                u[VP - 1] = pack2(u4.z, u4.w);
+                v[0] = pack2(v4.x, v4.y);
+                v[VP - 1] = pack2(v4.z, v4.w);
+            }
         } else {
             const float2 h2 = *reinterpret_cast<const float2 *>(p);
             const float2 u2 = *reinterpret_cast<const float2 *>(p + C::BW * CR);
@@ -271,7 +305,7 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
             u[0] = pack2(u2.x, u2.y);
             v[0] = pack2(v2.x, v2.y);
         }
-        if (EDGE) stream_ghosts<VP>(h, u, v, gx0, nx);
+        if (EDGE) stream_ghosts<VP, SPLIT>(h, u, v, gx0, nx);
 #pragma unroll
         for (int j = 0; j < VP; ++j) c[j] = make_cell2(h[j], u[j], v[j], k2);
     };
@@ -279,14 +313,15 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
     long long orow = (long long)ya * pitch + gx0;
     auto store_next = [&](const F2(&oh)[VP], const F2(&ou)[VP], const F2(&ov)[VP]) {
         if (stores && ok) {
-            store_cells<VP>(oH + orow, oh);
-            store_cells<VP>(oU + orow, ou);
-            store_cells<VP>(oV + orow, ov);
+            store_cells<VP, SPLIT>(oH + orow, oh);
+            store_cells<VP, SPLIT>(oU + orow, ou);
+            store_cells<VP, SPLIT>(oV + orow, ov);
 #pragma unroll
             for (int p = 0; p < VP; ++p) {
                 float a, b;
                 unpack2(oh[p], a, b);
-                bad |= (gx0 + 2 * p < nx && !(a > 0.0f)) || (gx0 + 2 * p + 1 < nx && !(b > 0.0f));
+                const int j0 = SPLIT ? p : 2 * p, j1 = SPLIT ? p + VP : 2 * p + 1;
+                bad |= (gx0 + j0 < nx && !(a > 0.0f)) || (gx0 + j1 < nx && !(b > 0.0f));
             }
         }
         orow += pitch;
@@ -308,8 +343,8 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
 #pragma unroll
         for (int p = 0; p < VP; ++p) u[p] = yface_flux2(c[p], n[p], k2);
         F2 oh[VP], ou[VP], ov[VP];
-        stream_update<VP>(c, d, u, k2, oh, ou, ov);
-        if (EDGE) stream_ghosts<VP>(oh, ou, ov, gx0, nx);
+        stream_update<VP, SPLIT>(c, d, u, k2, oh, ou, ov);
+        if (EDGE) stream_ghosts<VP, SPLIT>(oh, ou, ov, gx0, nx);
 #pragma unroll
         for (int p = 0; p < VP; ++p) m[p] = make_cell2(oh[p], ou[p], ov[p], k2);
     };
@@ -321,7 +356,7 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
 #pragma unroll
         for (int p = 0; p < VP; ++p) u2[p] = yface_flux2(c2[p], n2[p], k2);
         F2 oh[VP], ou[VP], ov[VP];
-        stream_update<VP>(c2, d2, u2, k2, oh, ou, ov);
+        stream_update<VP, SPLIT>(c2, d2, u2, k2, oh, ou, ov);
         store_next(oh, ou, ov);
     };
 
@@ -351,7 +386,7 @@ __device__ __forceinline__ bool stream_segment(StreamWarp<VP, LO, NO, CR, NSLOT,
 #pragma unroll
             for (int p = 0; p < VP; ++p) dB1[p] = yface_flux2(A1[p], B1[p], k2);
             F2 oh[VP], ou[VP], ov[VP];
-            stream_update<VP>(A1, dA1, dB1, k2, oh, ou, ov);
+            stream_update<VP, SPLIT>(A1, dA1, dB1, k2, oh, ou, ov);
             store_next(oh, ou, ov);
 #pragma unroll
             for (int p = 0; p < VP; ++p) {
