@@ -66,16 +66,14 @@ struct LearnCfg {
     static constexpr int STRIP = PXB * 16;   // one 8-channel strip of a ring row, bytes
     static constexpr int X0_ROW = 2 * STRIP; // 16 channels
     static constexpr int A_ROW = 4 * STRIP;  // 32 channels
-    // LW_SLOTS: group 0 writes the Lax-Wendroff row t in tick t and group 1
-    // reads it in tick t+6; group 0 reuses the slot in tick t+9, after its
-    // tick-(t+8) wait on layer 2's batch t+7, which follows group 1's whole
-    // tick t+6 (so 9 slots: group 0 does not wait on layer 3)
-    static constexpr int RING = 2, LW_SLOTS = 9;
+    // LW_SLOTS: a thread of group 0 writes its pixel of the Lax-Wendroff
+    // row t in tick t and reads it back in tick t+6 (rows t-6 .. t live)
+    static constexpr int RING = 2, LW_SLOTS = 7;
     static constexpr int NCW = 4 * NH * NG;  // compute warps; one more issues the MMAs
     static constexpr int THREADS = (NCW + 1) * 32;
-    // hidden channels per epilogue thread: group 0 (which also runs the
-    // Lax-Wendroff row) takes C0, group 1 (which also runs the output stage)
-    // the rest
+    // layer 1's channels per epilogue thread: group 0 (which also runs the
+    // Lax-Wendroff row and the output stage) takes C0, group 1 the rest;
+    // group 1 also takes all 32 channels of layer 2
     static constexpr int C0 = NG == 1 ? 32 : SWE_LEARN_C0;
     static constexpr int C1 = 32 - C0;
     static_assert(C0 % 8 == 0 && C0 >= 0 && C0 <= 32 && (NG == 2 || C0 == 32), "hidden channel split in 8-channel strips");
@@ -118,9 +116,11 @@ struct LearnArgs {
 
 // mbarriers (shared memory, in this order).  Each advances one phase per
 // batch; no barrier runs two phases ahead of a waiter, because every
-// arrival for batch t+1 follows its warp's wait on batch t.  B_RDY3 and B_L3
-// concern group 1 only (the output stage); group 0's part of layer 3's
-// input is published on B_RDY2, which the MMA warp waits for first.
+// arrival for batch t+1 follows its warp's wait on batch t.  B_RDY2 and B_L2
+// concern group 1 only (layer 2's epilogue), B_RDY3 and B_L3 group 0 only
+// (the output stage); the MMA warp waits for B_RDY1, B_RDY2 and B_RDY3 in
+// turn, so each layer's MMAs also follow the epilogue that wrote their
+// input row.
 enum { B_RDY1 = 0, B_RDY2 = 1, B_RDY3 = 2, B_L1 = 3, B_L2 = 4, B_L3 = 5, B_FIN = 6, B_COUNT = 7 };
 
 __device__ __forceinline__ void named_bar_sync(int id, int count)
@@ -251,19 +251,24 @@ template <int CPT>
 __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bias, unsigned char *dst, int strip,
                                                 bool valid)
 {
-    float v[CPT];
-    tmem_load<CPT>(taddr, v);
-    arm<CPT, false>(taddr, bias);  // completes under the activations
+    if constexpr (CPT == 32) {  // 16 columns at a time (registers)
+        hidden_epilogue<16>(taddr, bias, dst, strip, valid);
+        hidden_epilogue<16>(taddr + 16, bias + 16, dst + 2 * strip, strip, valid);
+    } else {
+        float v[CPT];
+        tmem_load<CPT>(taddr, v);
+        arm<CPT, false>(taddr, bias);  // completes under the activations
 #pragma unroll
-    for (int c = 0; c < CPT / 8; ++c) {
-        float y[8];
+        for (int c = 0; c < CPT / 8; ++c) {
+            float y[8];
 #pragma unroll
-        for (int k = 0; k < 8; k += 2) gelu_f2(v[8 * c + k], v[8 * c + k + 1], y[k], y[k + 1]);
-        const uint4 o = make_uint4(pack_bf16x2(y[0], y[1]), pack_bf16x2(y[2], y[3]), pack_bf16x2(y[4], y[5]),
-                                   pack_bf16x2(y[6], y[7]));
-        *reinterpret_cast<uint4 *>(dst + c * strip) = valid ? o : zero4();
+            for (int k = 0; k < 8; k += 2) gelu_f2(v[8 * c + k], v[8 * c + k + 1], y[k], y[k + 1]);
+            const uint4 o = make_uint4(pack_bf16x2(y[0], y[1]), pack_bf16x2(y[2], y[3]), pack_bf16x2(y[4], y[5]),
+                                       pack_bf16x2(y[6], y[7]));
+            *reinterpret_cast<uint4 *>(dst + c * strip) = valid ? o : zero4();
+        }
+        tc::wait_st();
     }
-    tc::wait_st();
 }
 
 // Copies the per-tap B images of one layer (global; block (tap, s) is
@@ -310,8 +315,8 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         mbar_init(bars + B_RDY1, C::NCW);
-        mbar_init(bars + B_RDY2, C::NCW);
-        mbar_init(bars + B_RDY3, C::NCW - C::PX / 32);  // group 1: the output stage
+        mbar_init(bars + B_RDY2, C::NCW - C::PX / 32);  // group 1: layer 2's epilogue
+        mbar_init(bars + B_RDY3, C::PX / 32);            // group 0: the output stage
         mbar_init(bars + B_L1, 1);
         mbar_init(bars + B_L2, 1);
         mbar_init(bars + B_L3, 1);
@@ -422,8 +427,8 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
         // ------------------------------------------------------------------
         // Compute warps.  Warp w reads TMEM lanes 32 (w % 4) .. +31: pixel
         // px = 128 hh + 32 q + lane of half hh, channel group g.  Group 0
-        // (PX threads, one per pixel) also runs the Lax-Wendroff step, group
-        // 1 the output stage and the mass sums.
+        // (PX threads, one per pixel) also runs the Lax-Wendroff step, the
+        // output stage and the mass sums; group 1 all of layer 2's epilogue.
         // ------------------------------------------------------------------
         const int q = warp & 3, hh = (warp >> 2) % NH, g = warp / (4 * NH);
         const int px = 128 * hh + 32 * q + lane;
@@ -432,9 +437,10 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
         // this thread's accumulator columns (block 0) of each layer
         const int ch = g == 0 ? 0 : C::C0;  // this thread's first hidden channel
         const uint32_t t1 = tmem + tl + C::ACC1 + hh * 96 + ch;
-        const uint32_t t2 = tmem + tl + C::ACC2 + hh * 96 + ch;
         const uint32_t t3 = tmem + tl + C::ACC3 + hh * 48;
-        const int sw = (ch / 8) * C::STRIP + (px + 1) * 16;  // ring offset of this thread's strips
+        const int sw = (ch / 8) * C::STRIP + (px + 1) * 16;  // ring offset of this thread's layer-1 strips
+        const uint32_t t2a = tmem + tl + C::ACC2 + hh * 96;   // layer 2, all 32 channels (group 1)
+        const int sw2 = (px + 1) * 16;
         // the hidden-layer epilogue with this group's channel count
         auto epilogue = [&](uint32_t taddr, const float *bias, unsigned char *dst, bool valid) {
             if (g == 0) {
@@ -495,15 +501,16 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
                     arm_hidden(t1 + b * 32, sBias + ch);
-                    arm_hidden(t2 + b * 32, sBias + 32 + ch);
-                    if (!lw_thread) {
+                    if (lw_thread) {
                         tc::st_x4_async(t3 + b * 16, sBias + 64);
                         tc::wait_st();
+                    } else {
+                        arm<32>(t2a + b * 32, sBias + 32);
                     }
                 }
                 double hs = 0.0;  // this pixel's h corrections: FP32 sums of 16 rows, added in FP64
                 float hs16 = 0.0f;
-                int lws = 0;  // lw ring slot of row t (t mod 9)
+                int lws = 0;  // lw ring slot of row t (t mod 7)
 #pragma unroll 1
                 for (int t = 0; t < T; ++t, lws = lws == C::LW_SLOTS - 1 ? 0 : lws + 1) {
                     const uint32_t parW = (nb + (uint32_t)t - 1u) & 1u;  // batch t-1
@@ -575,16 +582,19 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                     if (r1 >= 0 && r1 < H)
                         epilogue(t1 + mod3(r1) * 32, sBias + ch, sA1 + (r1 & 1) * C::A_ROW + sw, inside);
                     if (publish_t) publish(bars + B_RDY1, lane);
-                    // ---- E2 of row t-4 ----
-                    if (t >= 1) wait(bars + B_L2, parW);
-                    const int r2 = t - 4;
-                    if (r2 >= 0 && r2 < H)
-                        epilogue(t2 + mod3(r2) * 32, sBias + 32 + ch, sA2 + (r2 & 1) * C::A_ROW + sw, inside);
-                    if (publish_t) publish(bars + B_RDY2, lane);
-                    // ---- E3: corrected row t-6 ----
-                    if (!lw_thread && t >= 1) wait(bars + B_L3, parW);
+                    // ---- E2 of row t-4 (group 1) ----
+                    if (!lw_thread) {
+                        if (t >= 1) wait(bars + B_L2, parW);
+                        const int r2 = t - 4;
+                        if (r2 >= 0 && r2 < H)
+                            hidden_epilogue<32>(t2a + mod3(r2) * 32, sBias + 32, sA2 + (r2 & 1) * C::A_ROW + sw2,
+                                                C::STRIP, inside);
+                        if (publish_t) publish(bars + B_RDY2, lane);
+                    }
+                    // ---- E3: corrected row t-6 (group 0) ----
+                    if (lw_thread && t >= 1) wait(bars + B_L3, parW);
                     const int r3 = t - 6;
-                    if (!lw_thread && r3 >= 0 && r3 < H) {
+                    if (lw_thread && r3 >= 0 && r3 < H) {
                         // only columns 0..2 of a layer-3 block are outputs
                         // (the padding columns are never read): four
                         // columns are read and re-armed
@@ -595,7 +605,7 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                         tc::st_x4_async(ta, sBias + 64);
                         const float v[3] = {__uint_as_float(v4[0]), __uint_as_float(v4[1]), __uint_as_float(v4[2])};
                         if (inside) {
-                            const int s3 = lws >= 6 ? lws - 6 : lws + 3;  // (t - 6) mod 9
+                            const int s3 = lws >= 6 ? lws - 6 : lws + 1;  // (t - 6) mod 7
                             const float *lw = sLW + s3 * 3 * C::PX;
                             const long long o = (long long)r3 * pitch + px;
                             dst[o] = __fmaf_rn(v[0], a.os_h, lw[px]);
@@ -609,21 +619,16 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                         }
                         tc::wait_st();
                     }
-                    if (!lw_thread && publish_t) publish_tmem(bars + B_RDY3, lane);
+                    if (lw_thread && publish_t) publish_tmem(bars + B_RDY3, lane);
                 }
                 nb += (uint32_t)(T - 1);
                 // ---- mass projection: the mean h correction becomes the pending offset ----
-                // (group 1 holds the sums and wrote the corrected rows; the
-                // barrier also orders those writes before group 0 reads
-                // them as the next step's input)
-                if (!lw_thread) {
+                if (lw_thread) {
                     double s = hs;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) sRed[warp - 4 * NH] = s;
-                }
-                named_bar_sync(2, C::NCW * 32);
-                if (lw_thread) {
+                    if (lane == 0) sRed[warp] = s;
+                    named_bar_sync(1, C::PX);
                     double tot = 0.0;
                     for (int w = 0; w < 4 * NH; ++w) tot += sRed[w];
                     m = a.project ? (float)(tot / ((double)W * (double)H)) : 0.0f;
