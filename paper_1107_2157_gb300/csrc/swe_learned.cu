@@ -578,10 +578,12 @@ __global__ void __launch_bounds__(LearnCfg<NH, NG>::THREADS, 1) learned_step_ker
                     }
                     // ---- E1 of row t-2 (completed by batch t-1) ----
                     // Its a1 slot was last read by layer 2's batch t-2.  A
-                    // commit tracks every MMA its thread issued before it,
-                    // so the wait on layer 1's batch t-1 (issued after layer
-                    // 2's batch t-2) also covers that read: group 0 needs no
-                    // wait on layer 2.  Likewise layer 2's wait on batch t-1
+                    // commit tracks every MMA its thread issued before it
+                    // (one lane issues them all: elect.sync on the converged
+                    // MMA warp elects the same lane every time), so the wait
+                    // on layer 1's batch t-1 (issued after layer 2's batch
+                    // t-2) also covers that read: group 0 needs no wait on
+                    // layer 2.  Likewise layer 2's wait on batch t-1
                     // covers layer 3's batch t-2, the last reader of the a2
                     // slot that E2 rewrites.
                     if (t >= 1) wait(bars + B_L1, parW);
