@@ -74,9 +74,10 @@ struct LearnCfg {
     // layer 1's channels per epilogue thread: group 0 (which also runs the
     // Lax-Wendroff row and the output stage) takes C0, group 1 the rest;
     // group 1 also takes all 32 channels of layer 2
-    static constexpr int C0 = NG == 1 ? 32 : SWE_LEARN_C0;
+    static_assert(NG == 2, "two compute groups: group 0 the Lax-Wendroff row and the output stage, group 1 layer 2");
+    static constexpr int C0 = SWE_LEARN_C0;
     static constexpr int C1 = 32 - C0;
-    static_assert(C0 % 8 == 0 && C0 >= 0 && C0 <= 32 && (NG == 2 || C0 == 32), "hidden channel split in 8-channel strips");
+    static_assert(C0 % 8 == 0 && C0 >= 0 && C0 <= 32, "layer-1 channel split in 8-channel strips");
     // Weight images: per layer, rotation rho (0..2), kx, K step s, a 16 x 3C
     // K-major B operand [K core 2][N core 3C/8][8 x 16 B].
     static constexpr size_t IMG1 = 2 * 12 * 128, IMG2 = 2 * 12 * 128, IMG3 = 2 * 6 * 128;
