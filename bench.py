@@ -127,8 +127,9 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# Sources a step kernel's arithmetic and staging come from (its DRAM traffic
-# is reported only while they are unchanged since the counters were taken).
+# Sources a kernel's arithmetic and staging come from (its DRAM traffic and
+# pipe counters are reported only while they are unchanged since the
+# counters were taken).
 KERNEL_SOURCES = {
     "lw_tb2_kernel<float>": ("paper_1107_2157_gb300/csrc/swe_temporal.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
                              "paper_1107_2157_gb300/csrc/swe_device.cuh"),
@@ -143,6 +144,9 @@ KERNEL_SOURCES = {
                                "paper_1107_2157_gb300/csrc/swe_device.cuh"),
     "lw_packed_kernel": ("paper_1107_2157_gb300/csrc/swe_packed.cu", "paper_1107_2157_gb300/csrc/swe_tile.cuh",
                          "paper_1107_2157_gb300/csrc/swe_device.cuh"),
+    "learned_step_kernel<2,2>": ("paper_1107_2157_gb300/csrc/swe_learned.cu", "paper_1107_2157_gb300/csrc/swe_tc.cuh",
+                                 "paper_1107_2157_gb300/csrc/swe_gelu.cuh", "paper_1107_2157_gb300/csrc/swe_views.cuh",
+                                 "paper_1107_2157_gb300/csrc/swe_device.cuh"),
 }
 # swe_kernel value -> (kernel name, algorithmic bytes per cell-update of its state layout)
 STEP_KERNELS = {1: ("lw_naive_kernel<float>", 24), 2: ("lw_tiled_kernel<float>", 24),
@@ -171,6 +175,22 @@ def traffic_per_launch(kernel_name, cells):
     if kernel_name not in KERNEL_SOURCES or d.get("source_hash") != kernel_source_hash(kernel_name):
         return None
     return d["bytes_per_cell"] * cells * d.get("steps_per_launch", 1)
+
+
+def kernel_counters(kernel_name):
+    """The committed ncu counters of the fused learned step
+    (profiles/learned_kernel.json), if they were taken on the current kernel
+    source; else None."""
+    path = os.path.join(ROOT, "profiles", "learned_kernel.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel_name]
+    except Exception:
+        return None
+    if kernel_name not in KERNEL_SOURCES or d.get("source_hash") != kernel_source_hash(kernel_name):
+        return None
+    return {k: d[k] for k in ("tensor_pipe_pct", "issue_active_pct", "warp_instructions_per_cell_step",
+                              "dram_bytes_per_cell_step", "duration_ms", "workload", "command")}
 
 
 class ClockSampler:
@@ -777,7 +797,10 @@ def run_learned(args):
                     "speedup_vs_plain_at_equal_median_error": star_med["t_s"] / t_learned,
                     "speedup_vs_plain_fine_1024": t_fine / t_learned, "fallback_rate": fallback_rate,
                     "coarse_cell_updates_per_s": n * nc * nc * 64 / t_learned,
-                    "fine_equivalent_cell_updates_per_s": fine_updates / t_learned},
+                    "fine_equivalent_cell_updates_per_s": fine_updates / t_learned,
+                    # the serving is one launch of one kernel: its share is all of it
+                    "kernels": {"learned_step_kernel<2,2>": {
+                        "share": 1.0, "counters": kernel_counters("learned_step_kernel<2,2>")}}},
     }
     print(json.dumps(line), flush=True)
 
